@@ -1,0 +1,105 @@
+/*
+ * CPU ORACLE for Local Directional Pattern (LDP) and Local Binary Pattern (LBP)
+ * extraction -- TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow, literal restatement of the method of "An Acceleration Scheme
+ * to the Local Directional Pattern" (Ayami & Shabat, arXiv:1810.11518):
+ *   Sec. 2.1          LBP codes, 256-bin histograms
+ *   Sec. 2.2.1, Eq. 1 eight Kirsch compass responses (3x3 correlation)
+ *   Sec. 2.2.2, Eq. 2-3 LDP code: bits of the k most outstanding responses
+ *   Sec. 2.2.3, Eq. 4-6 code histograms / feature vector
+ *   Sec. 2.3, Eq. 7-29  the paper's ALDP column-sum scheme (aldp.c)
+ * It shares no code, header, table or helper with the CUDA library; only the
+ * test suite, the smoke check and the benchmark's CPU-baseline leg may call it.
+ *
+ * Readings taken where the paper is silent or garbled:
+ *   - x is the row, y the column; Eq. 1 is a correlation with mask M_i
+ *     (the printed "M_1" is read as M_i).
+ *   - M_0 is East and the masks run counter-clockwise (M_1 = NE, M_2 = N, ...,
+ *     M_7 = SE); this orientation is the one Eqs. 22-29 reproduce.
+ *   - "most outstanding" = largest |m_i|; exactly k bits are set, ties in
+ *     |m_i| go to the lower direction index.
+ *   - Only interior pixels (1 <= x <= H-2, 1 <= y <= W-2) get a code and are
+ *     counted; the compact histogram orders the C(8,k) codes by value.
+ *   - Regions: row band ri covers [floor(ri*H/R), floor((ri+1)*H/R)), column
+ *     band rj covers [floor(rj*W/C), floor((rj+1)*W/C)), in image
+ *     coordinates; region (ri, rj) is stored at (ri*C + rj) * nbins.
+ *   - LBP: bit j is set when neighbour p_j >= centre, p_0..p_7 taken
+ *     counter-clockwise from East like the masks.
+ * All counters are uint32.
+ */
+#ifndef ORACLE_LDP_H
+#define ORACLE_LDP_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* The eight masks, M_i(row, col), rows top to bottom (Sec. 2.2.1). */
+void oracle_kirsch_mask(int i, int32_t out3x3[9]);
+
+/* m_0..m_7 at interior pixel (x, y) by Eq. 1. */
+void oracle_responses(const uint8_t *img, int H, int W, int pitch, int x, int y, int32_t m[8]);
+
+/* Eq. 2-3: stable sort of 0..7 by |m_i| descending, first k indices set. */
+int oracle_code_from_responses(const int32_t m[8], int k);
+
+/* LBP label at interior pixel (x, y) (Sec. 2.1). */
+int oracle_lbp_code(const uint8_t *img, int H, int W, int pitch, int x, int y);
+
+/* Codes for interior pixels x in [x0,x1), y in [y0,y1) (image coordinates).
+ * Code of (x, y) goes to codes[(x - x0) * code_pitch + (y - y0)].
+ * mode: 0 = LDP with this k, 1 = LBP (k ignored).  Returns 0 or -1. */
+int oracle_codes_rect(const uint8_t *img, int H, int W, int pitch, int mode, int k,
+                      int x0, int x1, int y0, int y1, uint8_t *codes, int code_pitch);
+
+/* Number of compact bins C(8,k), and the ascending list of codes with
+ * popcount k (Eq. 6 ordering).  list may be NULL. */
+int oracle_compact_codes(int k, int *list);
+
+/* Position of `code` in the compact list for k, or -1. */
+int oracle_bin_of_code(int code, int k);
+
+/* Region bounds [lo, hi) of band b among nb bands over n pixels. */
+void oracle_band(int n, int nb, int b, int *lo, int *hi);
+
+/* Region histograms from a full interior code map (code of (x,y) at
+ * codes[(x-1)*code_pitch + (y-1)]).  nbins_k = 0: 256 raw bins per region;
+ * 1..7: compact C(8,k) bins.  hist is overwritten (R*C*nbins uint32). */
+int oracle_region_hist(const uint8_t *codes, int H, int W, int code_pitch, int R, int C,
+                       int nbins_k, uint32_t *hist);
+
+/* Whole path for one image: codes (optional, may be NULL) + region hists.
+ * mode 0 = LDP(k), 1 = LBP; compact selects C(8,k) bins (LDP only). */
+int oracle_extract(const uint8_t *img, int H, int W, int pitch, int mode, int k, int R, int C,
+                   int compact, uint32_t *hist, uint8_t *codes, int code_pitch);
+
+/* The same for n images, spread over nthreads host threads (one image per
+ * thread at a time).  Image i: img_base + img_off[i], (H[i], W[i], pitch[i]);
+ * hist at hist_base + hist_off[i] (uint32 elements); codes at
+ * codes_base + code_off[i] with code_pitch[i] when codes_base != NULL. */
+int oracle_extract_batch(int n, const uint8_t *img_base, const int64_t *img_off, const int *H,
+                         const int *W, const int *pitch, int mode, int k, int R, int C, int compact,
+                         uint32_t *hist_base, const int64_t *hist_off, uint8_t *codes_base,
+                         const int64_t *code_off, const int *code_pitch, int nthreads);
+
+/* ---- the paper's accelerated scheme (aldp.c) ---- */
+
+/* m_0..m_7 at (x, y) from the fifteen column sums A0..A14 (Eqs. 7-29). */
+void aldp_responses(const uint8_t *img, int H, int W, int pitch, int x, int y, int32_t m[8]);
+
+/* m_i = 8*S3_i - 3*S8 from ring sums (the identity the GPU path uses). */
+void ringsum_responses(const uint8_t *img, int H, int W, int pitch, int x, int y, int32_t m[8]);
+
+/* Eq. 2 by rank counting: bit i set iff fewer than k indices j beat i
+ * (|m_j| > |m_i|, or equal with j < i). */
+int rank_code_from_responses(const int32_t m[8], int k);
+
+/* Full-image LDP codes via ALDP responses + rank counting (CPU baseline). */
+int aldp_codes(const uint8_t *img, int H, int W, int pitch, int k, uint8_t *codes, int code_pitch);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
