@@ -1,0 +1,395 @@
+#!/usr/bin/env python
+"""LDP Mpixel/s (codes + region histograms), batched vs plain, % of HBM roofline.
+
+Workload (default): 4096 synthetic 640x490 uint8 images (seeds 0..4095,
+Gaussian blur sigma 3 + N(0, 8) noise), k = 3 LDP codes written to HBM fused
+with 7x6 region histograms of 56 bins (2352 uint32 per image).  One step is
+one batched pass over all 4096 images: a persistent, CUDA-graph-replayed
+launch through the C-ABI (ldp_batch_run).  Inputs (1.28 GB) and outputs
+(1.28 GB of codes) are far larger than the 129 MB L2, so no flush is needed
+between steps.
+
+Also reported on the same images: the plain per-image path (one
+ldp_region_hist call per image), the LBP batched path, an end-to-end number
+through host buffers (pinned H2D of the images + run + D2H of codes and
+histograms every step), the persistent kernel's roofline from CUDA events
+recorded around it inside the timed region, the SM clocks seen meanwhile,
+and the CPU oracle on a bounded sample on this host.
+
+`--impl reference` times the CPU oracle (the reference arm of this
+paper-only build) on the host cores, one bounded sample per step.
+
+Multi-GPU: images are independent, so N ranks each process their own 4096
+images (weak scaling, no collective on the data path); value = all pixels /
+max over ranks of the time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "LDP Mpixel/s (codes+region hist), batched vs plain, % of HBM roofline"
+UNIT = "Mpixel/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--images", type=int, default=4096)
+    ap.add_argument("--height", type=int, default=490)
+    ap.add_argument("--width", type=int, default=640)
+    ap.add_argument("--k", type=int, default=3)
+    ap.add_argument("--variant", type=int, default=-1, help="tile variant (-1: autotune cache or 0)")
+    ap.add_argument("--ctas-per-sm", type=int, default=0)
+    ap.add_argument("--cpu-sample", type=int, default=1024, help="images in the oracle CPU sample")
+    ap.add_argument("--no-extras", action="store_true", help="skip plain / LBP / e2e / CPU legs")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def algorithmic_bytes(Hs, Ws, hist_len):
+    Hs = np.asarray(Hs, dtype=np.int64)
+    Ws = np.asarray(Ws, dtype=np.int64)
+    return int((Hs * Ws).sum() + ((Hs - 2) * (Ws - 2)).sum() + len(Hs) * hist_len * 4)
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines: list[str] = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_oracle_sample(n_images, H, W, k, threads=None):
+    """The oracle, as it stands, on n images of the workload (host threads)."""
+    import oracle
+    import synth
+
+    threads = threads or max(1, os.cpu_count() or 1)
+    imgs = synth.batch(list(range(n_images)), H, W, 3.0, threads=threads)
+    offs = np.arange(n_images, dtype=np.int64) * (H * W)
+    t0 = time.perf_counter()
+    oracle.extract_batch(imgs.reshape(-1), offs, [H] * n_images, [W] * n_images, [W] * n_images, k=k, R=7, C=6,
+                         compact=True, threads=threads, want_codes=True)
+    dt = time.perf_counter() - t0
+    return n_images * H * W / dt / 1e6, dt, threads
+
+
+def run_reference(a):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    n = max(1, min(a.cpu_sample, a.images)) // 4 or 1
+    for _ in range(max(a.warmup, 0)):
+        cpu_oracle_sample(n, a.height, a.width, a.k)
+    vals, total = [], 0.0
+    for _ in range(a.steps):
+        v, dt, thr = cpu_oracle_sample(n, a.height, a.width, a.k)
+        vals.append(v)
+        total += dt
+    value = n * a.height * a.width * a.steps / total / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": a.gpus,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(1e3 * total / a.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic",
+        "config": {"workload": f"{a.images} x {a.width}x{a.height} uint8, k={a.k} LDP codes + 7x6 region hist (56 bins)",
+                   "sample_images_per_step": n},
+        "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": thr, "kind": "oracle",
+                         "sample": f"{n} images of {a.width}x{a.height} per step (seeds 0..{n - 1})"},
+        "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+        return
+    rank, world, local = dist_env()
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_1810_11518_gb300 as ldp
+    import synth
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+
+    n, H, W, k = a.images, a.height, a.width, a.k
+    nb = ldp.hist_bins(k)
+    hist_len = 7 * 6 * nb
+    lay = ldp.BatchLayout.build([H] * n, [W] * n, hist_len=hist_len)
+    seeds = np.arange(n, dtype=np.uint64) + np.uint64(rank * n)
+    # pinned host images, generated on the host cores
+    h_img = torch.empty(lay.img_bytes, dtype=torch.uint8, pin_memory=True)
+    synth.batch_into(h_img.numpy(), seeds, lay.Hs, lay.Ws, lay.pitches, lay.img_off, sigma=3.0)
+    d_img = h_img.to(dev, non_blocking=False)
+    d_codes = torch.zeros(lay.code_bytes, dtype=torch.uint8, device=dev)
+    d_hist = torch.zeros(n * hist_len, dtype=torch.int32, device=dev)
+    descs = lay.descs(d_img.data_ptr(), d_codes.data_ptr())
+    d_desc = torch.from_numpy(descs.view(np.uint8)).to(dev)
+    d_count = torch.tensor([n], dtype=torch.int32, device=dev)
+    pixels = lay.pixels
+    alg_bytes = algorithmic_bytes(lay.Hs, lay.Ws, hist_len)
+
+    plan = ldp.BatchPlan(n, pixels, k=k, regions=(7, 6), compact=True)
+    variant, cps = a.variant, a.ctas_per_sm
+    tuned = None
+    if variant < 0:
+        try:
+            from paper_1810_11518_gb300 import autotune
+
+            tuned = autotune.lookup(torch.cuda.get_device_name(dev), torch.cuda.get_device_properties(dev).multi_processor_count,
+                                    "batch", k, "hist+codes", H * W)
+        except Exception:
+            tuned = None
+        variant, cps = (tuned["variant"], tuned["ctas_per_sm"]) if tuned else (0, 0)
+    plan.set_config(variant, cps)
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if pg:
+            pg.barrier()
+        torch.cuda.synchronize(dev)
+
+    def max_over_ranks(x: float) -> float:
+        if not pg:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        return float(t.item())
+
+    # ---- warm-up ----
+    for _ in range(max(a.warmup, 3)):
+        plan.run(d_desc, d_count, d_hist)
+    torch.cuda.synchronize(dev)
+
+    gpu_uuid = str(torch.cuda.get_device_properties(dev).uuid)
+    clocks = ClockSampler(gpu_uuid if gpu_uuid.startswith("GPU-") else f"GPU-{gpu_uuid}")
+    clocks.start()
+    time.sleep(0.3)
+
+    # ---- timed: batched path ----
+    plan.enable_timing(a.steps)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(a.steps):
+        plan.run(d_desc, d_count, d_hist)
+    e1.record(stream)
+    barrier()
+    ms_total = max_over_ranks(e0.elapsed_time(e1))
+    ktimes = plan.kernel_times(a.steps)
+    ms_step = ms_total / a.steps
+    value = world * pixels * a.steps / (ms_total * 1e-3) / 1e6
+    k_ms = statistics.mean(ktimes) if ktimes else float("nan")
+    achieved_gbs = alg_bytes / (k_ms * 1e-3) / 1e9
+    peak, peak_src = load_peaks()
+
+    extras = {}
+    if not a.no_extras:
+        # ---- plain per-image path on the same images ----
+        imgs = [d_img[int(lay.img_off[i]):int(lay.img_off[i]) + H * int(lay.pitches[i])].view(H, int(lay.pitches[i]))[:, :W]
+                for i in range(n)]
+        cviews = [d_codes[int(lay.code_off[i]):int(lay.code_off[i]) + (H - 2) * int(lay.code_pitches[i])]
+                  .view(H - 2, int(lay.code_pitches[i]))[:, :W - 2] for i in range(n)]
+        hviews = [d_hist[i * hist_len:(i + 1) * hist_len] for i in range(n)]
+        ldp.set_plain_variant(0)
+
+        def plain_step():
+            for i in range(n):
+                ldp.region_hist(imgs[i], k=k, regions=(7, 6), compact=True, hist=hviews[i], codes_out=cviews[i],
+                                stream=stream)
+
+        plain_step()
+        psteps = max(2, min(10, a.steps // 20))
+        barrier()
+        e0.record(stream)
+        for _ in range(psteps):
+            plain_step()
+        e1.record(stream)
+        barrier()
+        pms = max_over_ranks(e0.elapsed_time(e1)) / psteps
+        extras["plain"] = {"value": round(world * pixels / (pms * 1e-3) / 1e6, 3), "unit": UNIT,
+                           "ms_per_step": round(pms, 4), "launches_per_step": 2 * n,
+                           "note": "one ldp_region_hist call (memset + fused kernel) per image"}
+        extras["batched_over_plain"] = round(pms / ms_step, 3)
+
+        # ---- LBP batched on the same images ----
+        lplan = ldp.BatchPlan(n, pixels, regions=(1, 1), lbp=True)
+        l_hist = torch.zeros(n * 256, dtype=torch.int32, device=dev)
+        ldescs = lay.descs(d_img.data_ptr(), d_codes.data_ptr())
+        ldescs["hist_offset"] = np.arange(n, dtype=np.uint64) * np.uint64(256)
+        l_desc = torch.from_numpy(ldescs.view(np.uint8)).to(dev)
+        for _ in range(3):
+            lplan.run(l_desc, d_count, l_hist)
+        lsteps = max(3, a.steps // 4)
+        barrier()
+        e0.record(stream)
+        for _ in range(lsteps):
+            lplan.run(l_desc, d_count, l_hist)
+        e1.record(stream)
+        barrier()
+        lms = max_over_ranks(e0.elapsed_time(e1)) / lsteps
+        extras["lbp_batched"] = {"value": round(world * pixels / (lms * 1e-3) / 1e6, 3), "unit": UNIT,
+                                 "ms_per_step": round(lms, 4), "hist": "256 bins, whole image"}
+        lplan.close()
+        del l_hist
+
+    # ---- end to end through host buffers: H2D images, run, D2H codes + hist ----
+    h_codes = torch.empty(lay.code_bytes, dtype=torch.uint8, pin_memory=True)
+    h_hist = torch.empty(n * hist_len, dtype=torch.int32, pin_memory=True)
+
+    def e2e_step():
+        d_img.copy_(h_img, non_blocking=True)
+        plan.run(d_desc, d_count, d_hist)
+        h_codes.copy_(d_codes, non_blocking=True)
+        h_hist.copy_(d_hist, non_blocking=True)
+
+    for _ in range(3):
+        e2e_step()
+    esteps = max(3, a.steps // 10)
+    barrier()
+    e0.record(stream)
+    for _ in range(esteps):
+        e2e_step()
+    e1.record(stream)
+    barrier()
+    ems = max_over_ranks(e0.elapsed_time(e1)) / esteps
+    e2e = {"value": round(world * pixels / (ems * 1e-3) / 1e6, 3), "unit": UNIT,
+           "h2d_bytes_per_step": int(h_img.numel()), "d2h_bytes_per_step": int(h_codes.numel() + 4 * h_hist.numel()),
+           "ms_per_step": round(ems, 4)}
+
+    clk = clocks.stop()
+
+    # ---- correctness spot check of the timed output (cheap): masses ----
+    hsum = d_hist.view(n, hist_len).sum(dim=1)
+    mass_ok = bool((hsum == (H - 2) * (W - 2)).all().item())
+
+    cpu = None
+    if rank == 0 and not a.no_extras and a.cpu_sample > 0:
+        v, dt, thr = cpu_oracle_sample(min(a.cpu_sample, n), H, W, k)
+        cpu = {"value": round(v, 3), "unit": UNIT, "cores": thr, "kind": "oracle",
+               "sample": f"{min(a.cpu_sample, n)} of the {n} images (seeds 0..{min(a.cpu_sample, n) - 1}), "
+                         f"codes + 7x6 hist, {dt:.1f} s"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": f"{n} x {W}x{H} uint8 images per GPU (seeds 0..{n - 1}, sigma 3), k={k} LDP "
+                                   f"codes + 7x6 region histograms ({nb} bins), batched persistent graph launch",
+                       "images": n, "height": H, "width": W, "k": k, "regions": [7, 6],
+                       "variant": ldp.variant_name(variant), "ctas_per_sm": cps,
+                       "autotuned": bool(tuned), "l2": "inputs+outputs 2.6 GB >> 129 MB L2, no flush",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": {"bound": "hbm", "achieved": round(achieved_gbs, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved_gbs / peak, 4), "traffic": None,
+                         "kernel": "k_batch (persistent LDP codes + region hist)",
+                         "kernel_ms": round(k_ms, 4), "algorithmic_bytes_per_launch": alg_bytes,
+                         "peak_source": f"{peak_src} hbm_gbs"},
+            "e2e": e2e,
+            "gpu_launches": 3 * a.steps,
+            "clocks": clk,
+            "cpu_baseline": cpu,
+            "hist_mass_ok": mass_ok,
+        }
+        line.update(extras)
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if pg:
+        pg.barrier()
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,190 @@
+/*
+ * libldp -- Local Directional Pattern (LDP) and Local Binary Pattern (LBP)
+ * feature extraction on NVIDIA GB300 (sm_103a).
+ *
+ * Method: Ayami & Shabat, "An Acceleration Scheme to the Local Directional
+ * Pattern", arXiv:1810.11518.
+ *   Sec. 2.2.1, Eq. 1   eight Kirsch compass responses m_0..m_7 per pixel
+ *   Sec. 2.2.2, Eq. 2-3 LDP code: bits of the k most outstanding responses
+ *   Sec. 2.2.3, Eq. 4-6 code histograms (feature vectors), here per region
+ *   Sec. 2.1            LBP codes and 256-bin histograms (the comparison)
+ *   Sec. 3.2            windowed extraction, here an R x C grid of regions
+ *
+ * Conventions fixed by this library (the paper leaves them open):
+ *   - Images are uint8, row-major, H rows x W columns, row pitch >= W bytes.
+ *     x is the row, y the column; M_0 is East and the masks run
+ *     counter-clockwise (M_1 = NE, M_2 = N, ..., M_7 = SE); code bit i
+ *     belongs to mask i.  Eq. 1 is a correlation.
+ *   - Ranking is by |m_i|, exactly k bits are set, and equal |m_i| are
+ *     ranked by lower direction index first.
+ *   - Only interior pixels (1 <= x <= H-2, 1 <= y <= W-2) have a code and
+ *     are counted.  The code of (x, y) is stored at
+ *     codes[(x-1)*code_pitch + (y-1)]; code_pitch >= W-2.
+ *   - Region (ri, rj) of an R x C grid holds rows
+ *     [floor(ri*H/R), floor((ri+1)*H/R)) and columns
+ *     [floor(rj*W/C), floor((rj+1)*W/C)) of the image; its histogram is
+ *     stored at hist[(ri*C + rj)*nbins ...].  nbins is 256 (raw code
+ *     values) or, for LDP with compact = 1, C(8,k) bins ordered by ascending
+ *     code value (Eq. 6).  Counters are uint32.
+ *   - LBP bit j is set when neighbour p_j >= centre, p_0 = East,
+ *     counter-clockwise; 256 bins.
+ *
+ * Memory and streams: every image, code and histogram buffer is a device
+ * pointer owned by the caller.  Calls are asynchronous and ordered on the
+ * CUDA stream passed as `stream` (a cudaStream_t; NULL = legacy default
+ * stream); the caller synchronises before reading results.  Histogram
+ * buffers are overwritten (zeroed on the stream first).  The library owns
+ * only opaque batch plans.
+ *
+ * Errors: every entry point returns an ldp_status and never aborts or traps.
+ * LDP_EINVAL rejects bad arguments before anything is launched; CUDA launch
+ * or runtime errors give LDP_ECUDA.  ldp_last_error() returns a message for
+ * the calling thread's most recent failure.
+ *
+ * Alignment: any pointer and pitch are accepted.  16-byte aligned image and
+ * code buffers with pitches that are multiples of 16 take the fast path;
+ * other layouts are processed correctly by a slower byte-wise path.  There
+ * is no CPU fallback: the work always runs on the GPU.
+ */
+#ifndef LDP_H
+#define LDP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define LDP_API __attribute__((visibility("default")))
+#else
+#define LDP_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LDP_OK = 0,
+    LDP_EINVAL = 1,   /* invalid argument, nothing launched */
+    LDP_ECUDA = 2,    /* CUDA runtime / launch error */
+    LDP_ENOMEM = 3,   /* device or host allocation failed */
+    LDP_ETIMEOUT = 4, /* a bounded device-side wait gave up */
+    LDP_ENOTIMPL = 5  /* combination not supported */
+} ldp_status;
+
+/* R x C grid of regions (Sec. 3.2 windows); compact = 1 selects the C(8,k)
+ * bins of Eq. 6 for LDP, 0 the 256 raw code values.  R, C >= 1. */
+typedef struct {
+    int32_t R, C;
+    int32_t compact;
+} ldp_region_spec;
+
+/* One image of a batch, resident in device memory.  codes may be NULL (no
+ * code map for that image).  hist_offset counts uint32 elements from the
+ * d_hist pointer given to the batch run.  40 bytes, 8-byte aligned. */
+typedef struct {
+    const uint8_t *img;
+    int32_t H, W, pitch, code_pitch;
+    uint8_t *codes;
+    uint64_t hist_offset;
+} ldp_image_desc;
+
+/* ---- single image ---- */
+
+/* LDP codes (Eq. 1-3) of the interior of one image.
+ * d_img: H x W, row pitch `pitch` bytes.  k in [1,7].
+ * d_codes: (H-2) x (W-2), row pitch code_pitch >= W-2.
+ * EINVAL: NULL pointer, H < 3, W < 3, pitch < W, code_pitch < W-2, k out
+ * of range, H or W > 1<<20. */
+LDP_API int ldp_codes(const uint8_t *d_img, int H, int W, int pitch, int k, uint8_t *d_codes,
+              int code_pitch, void *stream);
+
+/* LDP codes fused with region histograms (Eq. 1-6): one launch computes
+ * the codes, optionally stores them (d_codes_or_null), and accumulates the
+ * R x C region histograms into d_hist (R*C*nbins uint32, overwritten).
+ * EINVAL as ldp_codes, plus R < 1, C < 1, compact not 0/1, d_hist NULL. */
+LDP_API int ldp_region_hist(const uint8_t *d_img, int H, int W, int pitch, int k, ldp_region_spec rs,
+                    uint32_t *d_hist, uint8_t *d_codes_or_null, int code_pitch, void *stream);
+
+/* LBP codes (Sec. 2.1) of the interior of one image; layout as ldp_codes. */
+LDP_API int lbp_codes(const uint8_t *d_img, int H, int W, int pitch, uint8_t *d_codes, int code_pitch,
+              void *stream);
+
+/* LBP codes fused with 256-bin region histograms (R x C regions). */
+LDP_API int lbp_region_hist(const uint8_t *d_img, int H, int W, int pitch, int R, int C, uint32_t *d_hist,
+                    uint8_t *d_codes_or_null, int code_pitch, void *stream);
+
+/* ---- batches of images of any sizes: one persistent launch ---- */
+
+typedef struct ldp_batch_plan ldp_batch_plan;
+
+#define LDP_PLAN_LBP 1u       /* plan runs LBP (k ignored, 256 bins) */
+#define LDP_PLAN_NO_GRAPH 2u  /* launch kernels directly instead of replaying a CUDA graph */
+
+/* Creates a plan for batches of up to max_images images holding up to
+ * max_pixels pixels in total.  The plan owns its device work-list scratch
+ * (allocated here) and a CUDA graph of its launches (built on first run).
+ * EINVAL: out NULL, max_images < 1, bad k / rs; ENOMEM on allocation
+ * failure. */
+LDP_API int ldp_batch_plan_create(ldp_batch_plan **out, int max_images, uint64_t max_pixels, int k,
+                          ldp_region_spec rs, unsigned flags);
+
+/* Runs the plan: the image count is read from device memory (*d_count,
+ * clamped to max_images), descriptors from d_descs[0..count), so one
+ * captured graph serves any count.  Each image's histogram
+ * (R*C*nbins uint32 at d_hist + hist_offset) is zeroed and accumulated;
+ * its codes are stored when desc.codes != NULL.  Images whose descriptor
+ * is invalid (H < 3, W < 3, pitch < W, NULL img, or codes with
+ * code_pitch < W-2) are skipped and flagged in the device status word.
+ * Stream-ordered; d_descs, d_count and d_hist must stay valid until the
+ * work completes.  ldp_batch_run requires an LDP plan, lbp_batch_run an
+ * LBP plan (EINVAL otherwise). */
+LDP_API int ldp_batch_run(ldp_batch_plan *plan, const ldp_image_desc *d_descs, const int *d_count,
+                  uint32_t *d_hist, void *stream);
+LDP_API int lbp_batch_run(ldp_batch_plan *plan, const ldp_image_desc *d_descs, const int *d_count,
+                  uint32_t *d_hist, void *stream);
+
+/* Kernel timing: after enable_timing(plan, capacity), each of the next
+ * `capacity` runs records a pair of CUDA events around its persistent
+ * kernel (inside the CUDA graph too, by updating the graph's event-record
+ * nodes).  kernel_times() waits for the recorded events, writes the
+ * elapsed milliseconds of up to `capacity` runs (in run order) to ms,
+ * stores their number in *count, and starts a new recording. */
+LDP_API int ldp_batch_plan_enable_timing(ldp_batch_plan *plan, int capacity);
+LDP_API int ldp_batch_plan_kernel_times(ldp_batch_plan *plan, float *ms, int capacity, int *count);
+
+/* Frees the plan's device scratch, events and graph (synchronises the device). */
+LDP_API int ldp_batch_plan_destroy(ldp_batch_plan *plan);
+
+/* Kernel configuration (tile shape / CTAs per SM) a plan uses; set by the
+ * autotuner.  variant in [0, ldp_num_variants()), ctas_per_sm 0 = as many
+ * as fit. */
+LDP_API int ldp_batch_plan_set_config(ldp_batch_plan *plan, int variant, int ctas_per_sm);
+LDP_API int ldp_num_variants(void);
+/* Short description of a variant ("r16w4" ...), static storage. */
+LDP_API const char *ldp_variant_name(int variant);
+/* Variant used by the single-image entry points (default 0). */
+LDP_API int ldp_set_plain_variant(int variant);
+
+/* ---- helpers ---- */
+
+/* Compact bins for k (Eq. 6): C(8,k), or -1 when k is outside [0,8]. */
+LDP_API int ldp_hist_bins(int k);
+
+/* Compact bin of an 8-bit code for k (its colex rank among the codes with
+ * popcount k, i.e. its position in ascending code order), or -1. */
+LDP_API int ldp_bin_of_code(int code, int k);
+
+/* Message for the calling thread's most recent failing call ("" if none). */
+LDP_API const char *ldp_last_error(void);
+
+/* Reads and clears the device status word (bit 0: a batch descriptor was
+ * rejected on the device).  Synchronises `stream`. */
+LDP_API int ldp_device_status(void *stream, int *out);
+
+/* Library version (major*10000 + minor*100 + patch). */
+LDP_API int ldp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LDP_H */

@@ -1,0 +1,267 @@
+"""LDP / LBP feature extraction on GB300 (sm_103a).
+
+Python face of libldp (include/ldp.h).  PyTorch provides device memory and
+streams; every pixel is processed by the library's CUDA kernels.  Images are
+``torch.uint8`` CUDA tensors of shape (H, W) whose rows may be padded
+(``stride(0)`` is the pitch, ``stride(1)`` must be 1).
+
+Method: Ayami & Shabat, arXiv:1810.11518 -- Kirsch responses (Eq. 1), the
+LDP code of the k largest |m_i| (Eq. 2-3, ties to the lower index), region
+histograms (Eq. 4-6, Sec. 3.2) and LBP (Sec. 2.1).
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+from math import comb
+
+import numpy as np
+
+from . import _abi
+from ._abi import LdpError, RegionSpec
+
+__all__ = ["codes", "region_hist", "lbp_codes", "lbp_region_hist", "hist_bins", "bin_of_code",
+           "BatchPlan", "BatchLayout", "DESC_DTYPE", "LdpError", "device_status", "num_variants",
+           "variant_name", "set_plain_variant", "load"]
+
+DESC_DTYPE = np.dtype([("img", "<u8"), ("H", "<i4"), ("W", "<i4"), ("pitch", "<i4"),
+                       ("code_pitch", "<i4"), ("codes", "<u8"), ("hist_offset", "<u8")])
+assert DESC_DTYPE.itemsize == 40
+
+
+def load():
+    """Loads libldp.so; raises if it is missing."""
+    return _abi.load()
+
+
+def _torch():
+    import torch
+
+    return torch
+
+
+def _stream(stream):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _img(img):
+    torch = _torch()
+    if not isinstance(img, torch.Tensor) or img.dtype != torch.uint8 or not img.is_cuda:
+        raise TypeError("image must be a torch.uint8 CUDA tensor")
+    if img.dim() != 2 or img.stride(1) != 1:
+        raise ValueError("image must be 2-D with unit column stride")
+    H, W = img.shape
+    return ctypes.c_void_p(img.data_ptr()), int(H), int(W), int(img.stride(0))
+
+
+def _alloc_codes(img, H, W, out):
+    torch = _torch()
+    if out is not None:
+        if out.dtype != torch.uint8 or not out.is_cuda or out.dim() != 2 or out.stride(1) != 1:
+            raise ValueError("out must be a 2-D uint8 CUDA tensor")
+        if tuple(out.shape) != (H - 2, W - 2):
+            raise ValueError(f"out must have shape {(H - 2, W - 2)}")
+        return out, int(out.stride(0))
+    pc = (W - 2 + 15) // 16 * 16
+    buf = torch.empty((H - 2, pc), dtype=torch.uint8, device=img.device)
+    return buf[:, :W - 2], pc
+
+
+def hist_bins(k: int) -> int:
+    return int(_abi.load().ldp_hist_bins(k))
+
+
+def bin_of_code(code: int, k: int) -> int:
+    return int(_abi.load().ldp_bin_of_code(code, k))
+
+
+def codes(img, k: int = 3, out=None, stream=None):
+    """LDP codes (Eq. 1-3) of the interior: uint8 tensor (H-2, W-2)."""
+    p, H, W, P = _img(img)
+    out, pc = _alloc_codes(img, H, W, out)
+    _abi.call("ldp_codes", p, H, W, P, k, ctypes.c_void_p(out.data_ptr()), pc, _stream(stream))
+    return out
+
+
+def region_hist(img, k: int = 3, regions=(1, 1), compact: bool = True, with_codes: bool = True,
+                hist=None, codes_out=None, stream=None):
+    """Fused LDP codes + R x C region histograms (Eq. 1-6).
+
+    Returns (hist int32 tensor (R, C, nbins) holding uint32 counts, codes or None)."""
+    torch = _torch()
+    p, H, W, P = _img(img)
+    R, C = regions
+    nb = comb(8, k) if compact else 256
+    if hist is None:
+        hist = torch.empty((R, C, nb), dtype=torch.int32, device=img.device)
+    elif hist.numel() != R * C * nb or not hist.is_contiguous():
+        raise ValueError("hist must be a contiguous tensor of R*C*nbins int32")
+    cptr, pc, out = None, 0, None
+    if with_codes:
+        out, pc = _alloc_codes(img, H, W, codes_out)
+        cptr = ctypes.c_void_p(out.data_ptr())
+    _abi.call("ldp_region_hist", p, H, W, P, k, RegionSpec(R, C, int(compact)),
+              ctypes.c_void_p(hist.data_ptr()), cptr, pc, _stream(stream))
+    return hist, out
+
+
+def lbp_codes(img, out=None, stream=None):
+    """LBP codes (Sec. 2.1) of the interior: uint8 tensor (H-2, W-2)."""
+    p, H, W, P = _img(img)
+    out, pc = _alloc_codes(img, H, W, out)
+    _abi.call("lbp_codes", p, H, W, P, ctypes.c_void_p(out.data_ptr()), pc, _stream(stream))
+    return out
+
+
+def lbp_region_hist(img, regions=(1, 1), with_codes: bool = True, hist=None, codes_out=None, stream=None):
+    """Fused LBP codes + R x C region histograms of 256 bins."""
+    torch = _torch()
+    p, H, W, P = _img(img)
+    R, C = regions
+    if hist is None:
+        hist = torch.empty((R, C, 256), dtype=torch.int32, device=img.device)
+    cptr, pc, out = None, 0, None
+    if with_codes:
+        out, pc = _alloc_codes(img, H, W, codes_out)
+        cptr = ctypes.c_void_p(out.data_ptr())
+    _abi.call("lbp_region_hist", p, H, W, P, R, C, ctypes.c_void_p(hist.data_ptr()), cptr, pc, _stream(stream))
+    return hist, out
+
+
+def num_variants() -> int:
+    return int(_abi.load().ldp_num_variants())
+
+
+def variant_name(v: int) -> str:
+    return _abi.load().ldp_variant_name(v).decode()
+
+
+def set_plain_variant(v: int) -> None:
+    _abi.call("ldp_set_plain_variant", v)
+
+
+def device_status(stream=None) -> int:
+    out = ctypes.c_int(0)
+    _abi.call("ldp_device_status", _stream(stream), ctypes.byref(out))
+    return out.value
+
+
+@dataclass
+class BatchLayout:
+    """Host-side layout of n images packed in one flat uint8 buffer, their
+    code maps in another, and their histograms in one int32 buffer.  Pitches
+    are rounded up to 16 bytes so every row starts 16-byte aligned."""
+
+    Hs: np.ndarray
+    Ws: np.ndarray
+    pitches: np.ndarray
+    img_off: np.ndarray
+    code_pitches: np.ndarray
+    code_off: np.ndarray
+    hist_len: int
+    img_bytes: int
+    code_bytes: int
+
+    @staticmethod
+    def build(Hs, Ws, hist_len: int, align: int = 16) -> "BatchLayout":
+        Hs = np.asarray(Hs, dtype=np.int64)
+        Ws = np.asarray(Ws, dtype=np.int64)
+        pitches = (Ws + align - 1) // align * align
+        sizes = Hs * pitches
+        img_off = np.concatenate([[0], np.cumsum(sizes)[:-1]]).astype(np.int64)
+        cps = np.maximum((Ws - 2 + align - 1) // align * align, align)
+        csz = np.maximum(Hs - 2, 0) * cps
+        code_off = np.concatenate([[0], np.cumsum(csz)[:-1]]).astype(np.int64)
+        return BatchLayout(Hs, Ws, pitches, img_off, cps, code_off, int(hist_len),
+                           int(sizes.sum()), int(max(csz.sum(), 16)))
+
+    @property
+    def n(self) -> int:
+        return len(self.Hs)
+
+    @property
+    def pixels(self) -> int:
+        return int((self.Hs * self.Ws).sum())
+
+    def descs(self, img_base: int, code_base: int | None) -> np.ndarray:
+        d = np.zeros(self.n, dtype=DESC_DTYPE)
+        d["img"] = img_base + self.img_off
+        d["H"] = self.Hs
+        d["W"] = self.Ws
+        d["pitch"] = self.pitches
+        d["code_pitch"] = self.code_pitches
+        d["codes"] = (code_base + self.code_off) if code_base else 0
+        d["hist_offset"] = np.arange(self.n, dtype=np.uint64) * np.uint64(self.hist_len)
+        return d
+
+    def image(self, buf, i: int):
+        """View of image i inside a flat buffer (numpy or torch), shape (H, W)."""
+        o, H, W, P = int(self.img_off[i]), int(self.Hs[i]), int(self.Ws[i]), int(self.pitches[i])
+        return buf[o:o + H * P].reshape(H, P)[:, :W]
+
+    def codes(self, buf, i: int):
+        o, H, W, P = int(self.code_off[i]), int(self.Hs[i]), int(self.Ws[i]), int(self.code_pitches[i])
+        return buf[o:o + (H - 2) * P].reshape(H - 2, P)[:, :W - 2]
+
+
+class BatchPlan:
+    """A plan for one persistent launch over up to max_images images of any
+    sizes (the library's work list and CUDA graph live inside)."""
+
+    def __init__(self, max_images: int, max_pixels: int, k: int = 3, regions=(7, 6), compact: bool = True,
+                 lbp: bool = False, graph: bool = True):
+        self.lbp = lbp
+        self.k = k
+        self.regions = tuple(regions)
+        self.compact = bool(compact) and not lbp
+        self.nbins = comb(8, k) if self.compact else 256
+        flags = (_abi.LDP_PLAN_LBP if lbp else 0) | (0 if graph else _abi.LDP_PLAN_NO_GRAPH)
+        h = ctypes.c_void_p()
+        _abi.call("ldp_batch_plan_create", ctypes.byref(h), int(max_images), int(max_pixels), int(k),
+                  RegionSpec(self.regions[0], self.regions[1], int(self.compact)), flags)
+        self._h = h
+
+    @property
+    def hist_len(self) -> int:
+        return self.regions[0] * self.regions[1] * self.nbins
+
+    def set_config(self, variant: int, ctas_per_sm: int = 0) -> None:
+        _abi.call("ldp_batch_plan_set_config", self._h, int(variant), int(ctas_per_sm))
+
+    def run(self, d_descs, d_count, d_hist, stream=None) -> None:
+        """d_descs: device buffer of DESC_DTYPE records; d_count: device int32
+        holding the image count; d_hist: device int32 buffer (or None)."""
+        fn = "lbp_batch_run" if self.lbp else "ldp_batch_run"
+        hist_ptr = ctypes.c_void_p(d_hist.data_ptr()) if d_hist is not None else None
+        _abi.call(fn, self._h, ctypes.c_void_p(d_descs.data_ptr()), ctypes.c_void_p(d_count.data_ptr()),
+                  hist_ptr, _stream(stream))
+
+    def enable_timing(self, capacity: int) -> None:
+        """Record CUDA events around the persistent kernel of the next `capacity` runs."""
+        _abi.call("ldp_batch_plan_enable_timing", self._h, int(capacity))
+
+    def kernel_times(self, capacity: int = 1 << 16) -> list[float]:
+        """Milliseconds of the persistent kernel of each recorded run (waits for them)."""
+        buf = (ctypes.c_float * capacity)()
+        n = ctypes.c_int(0)
+        _abi.call("ldp_batch_plan_kernel_times", self._h, buf, capacity, ctypes.byref(n))
+        return [float(buf[i]) for i in range(n.value)]
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) and self._h.value:
+            _abi.load().ldp_batch_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

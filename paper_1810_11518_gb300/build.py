@@ -1,0 +1,86 @@
+"""Builds libldp.so (all CUDA sources, sm_103a) in-tree.
+
+Translation units are compiled in parallel: the common kernels, the C-ABI,
+and the tile-variant kernels (one object per entry of LDP_VARIANTS in
+csrc/ldp_launch.h).  Objects go to _build/, the library next to this file.
+"""
+from __future__ import annotations
+
+import concurrent.futures as cf
+import glob
+import os
+import re
+import shutil
+import subprocess
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+CSRC = os.path.join(HERE, "csrc")
+BUILD = os.path.join(HERE, "_build")
+LIB = os.path.join(HERE, "libldp.so")
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fvisibility=hidden", "-Xptxas", "-warn-spills"]
+
+
+def nvcc() -> str:
+    for cand in (os.environ.get("NVCC"), shutil.which("nvcc"), "/usr/local/cuda/bin/nvcc"):
+        if cand and os.path.exists(cand):
+            return cand
+    raise RuntimeError("nvcc not found")
+
+
+def variants() -> list[tuple[int, int, int]]:
+    with open(os.path.join(CSRC, "ldp_launch.h")) as f:
+        src = f.read()
+    m = re.search(r"#define LDP_VARIANTS\(X\)(.*)", src)
+    if not m:
+        raise RuntimeError("LDP_VARIANTS not found")
+    return [tuple(int(v) for v in t) for t in re.findall(r"X\((\d+),\s*(\d+),\s*(\d+)\)", m.group(1))]
+
+
+def _sources_mtime() -> float:
+    files = glob.glob(os.path.join(CSRC, "*")) + [os.path.join(ROOT, "include", "ldp.h"), __file__]
+    return max(os.path.getmtime(f) for f in files)
+
+
+def _compile(args: list[str]) -> tuple[list[str], int, str]:
+    p = subprocess.run(args, capture_output=True, text=True)
+    return args, p.returncode, p.stdout + p.stderr
+
+
+def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -> str:
+    """Compile every CUDA translation unit for sm_103a and link libldp.so."""
+    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _sources_mtime():
+        return LIB
+    os.makedirs(BUILD, exist_ok=True)
+    cc = nvcc()
+    inc = ["-I", os.path.join(ROOT, "include"), "-I", CSRC]
+    units = [
+        (os.path.join(CSRC, "ldp_common.cu"), os.path.join(BUILD, "ldp_common.o"), []),
+        (os.path.join(CSRC, "ldp_abi.cu"), os.path.join(BUILD, "ldp_abi.o"), []),
+    ]
+    for vid, rpw, nw in variants():
+        units.append((os.path.join(CSRC, "ldp_kernels.cu"), os.path.join(BUILD, f"ldp_kernels_v{vid}.o"),
+                      [f"-DLDP_VAR_ID={vid}", f"-DLDP_VAR_RPW={rpw}", f"-DLDP_VAR_NW={nw}"]))
+    cmds = [[cc] + ARCH + FLAGS + inc + defs + ["-c", src, "-o", obj] for src, obj, defs in units]
+    jobs = jobs or max(1, min(len(cmds), os.cpu_count() or 1))
+    with cf.ThreadPoolExecutor(jobs) as ex:
+        results = list(ex.map(_compile, cmds))
+    for args, rc, out in results:
+        if rc != 0:
+            raise RuntimeError("nvcc failed:\n" + " ".join(args) + "\n" + out)
+        if verbose and out.strip():
+            print(out)
+    tmp = LIB + f".{os.getpid()}.tmp"
+    link = [cc] + ARCH + ["-shared", "-o", tmp] + [obj for _, obj, _ in units]
+    p = subprocess.run(link, capture_output=True, text=True)
+    if p.returncode != 0:
+        raise RuntimeError("link failed:\n" + " ".join(link) + "\n" + p.stdout + p.stderr)
+    os.replace(tmp, LIB)
+    return LIB
+
+
+if __name__ == "__main__":
+    import sys
+
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))

@@ -1,0 +1,402 @@
+// C-ABI of libldp (declared in include/ldp.h): argument validation, error
+// reporting, single-image launches, batch plans with CUDA-graph replay.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "ldp_launch.h"
+
+namespace {
+
+thread_local std::string t_err;
+std::atomic<int> g_plain_variant{0};
+
+int fail(int code, const char* msg) {
+    t_err = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+    t_err = std::string(where) + ": " + cudaGetErrorName(e) + ": " + cudaGetErrorString(e);
+    return LDP_ECUDA;
+}
+
+int binom8(int r) {
+    if (r < 0 || r > 8) return -1;
+    int c = 1;
+    for (int i = 1; i <= r; ++i) c = c * (8 - r + i) / i;
+    return c;
+}
+
+int check_image(const void* img, int H, int W, int pitch) {
+    if (!img) return fail(LDP_EINVAL, "image pointer is NULL");
+    if (H < 3 || W < 3) return fail(LDP_EINVAL, "image must be at least 3x3");
+    if (H > (1 << 20) || W > (1 << 20)) return fail(LDP_EINVAL, "image side larger than 1<<20");
+    if (pitch < W) return fail(LDP_EINVAL, "pitch < W");
+    return LDP_OK;
+}
+
+int check_codes(const void* codes, int W, int code_pitch, bool required) {
+    if (!codes) return required ? fail(LDP_EINVAL, "codes pointer is NULL") : LDP_OK;
+    if (code_pitch < W - 2) return fail(LDP_EINVAL, "code_pitch < W-2");
+    return LDP_OK;
+}
+
+int check_regions(int R, int C) {
+    if (R < 1 || C < 1) return fail(LDP_EINVAL, "region grid must be at least 1x1");
+    if ((int64_t)R * (int64_t)C > (1 << 22)) return fail(LDP_EINVAL, "region grid larger than 1<<22 regions");
+    return LDP_OK;
+}
+
+int run_plain(int mode, const uint8_t* img, int H, int W, int pitch, int k, int R, int C, int compact,
+              uint32_t* hist, uint8_t* codes, int code_pitch, void* stream) {
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    ldp::JobArgs jb{img, H, W, pitch, codes, code_pitch, hist};
+    ldp::HistArgs hc{R, C, 256, 0};
+    if (hist) {
+        hc.nbins = (mode == 0 && compact) ? binom8(k) : 256;
+        hc.compact = (mode == 0 && compact) ? 1 : 0;
+        const size_t bytes = (size_t)R * (size_t)C * (size_t)hc.nbins * sizeof(uint32_t);
+        cudaError_t e = cudaMemsetAsync(hist, 0, bytes, s);
+        if (e != cudaSuccess) return cuda_fail(e, "zeroing the histogram");
+    }
+    cudaError_t e = ldp::launch_plain(mode, k, hist != nullptr, g_plain_variant.load(), jb, hc, s);
+    if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+    return LDP_OK;
+}
+
+}  // namespace
+
+struct ldp_batch_plan {
+    int mode = 0, k = 3;
+    ldp_region_spec rs{1, 1, 0};
+    unsigned flags = 0;
+    int max_images = 0, max_tiles = 0;
+    uint64_t max_pixels = 0;
+    int variant = 0, ctas_per_sm = 0;
+    int device = 0, num_sms = 0;
+    void* scratch = nullptr;
+    ldp::BatchScratch scr{};
+    cudaStream_t cap_stream = nullptr;
+    // graph cache
+    cudaGraphExec_t exec = nullptr;
+    cudaGraph_t graph = nullptr;  // kept alive: its event-record nodes address the exec's nodes
+    const void *g_descs = nullptr, *g_count = nullptr, *g_hist = nullptr;
+    int g_variant = -1, g_grid = 0;
+    // timing: event-record nodes around the persistent kernel
+    cudaEvent_t ph_start = nullptr, ph_end = nullptr;  // events the graph was captured with
+    cudaGraphNode_t node_start = nullptr, node_end = nullptr;
+    std::vector<cudaEvent_t> ev_start, ev_end;
+    int nrec = 0;
+};
+
+extern "C" {
+
+int ldp_version(void) { return 100; }
+
+const char* ldp_last_error(void) { return t_err.c_str(); }
+
+int ldp_hist_bins(int k) { return binom8(k); }
+
+int ldp_bin_of_code(int code, int k) {
+    if (code < 0 || code > 255 || k < 0 || k > 8) return -1;
+    if (__builtin_popcount((unsigned)code) != k) return -1;
+    // colex rank: sum over set bits b_1 < ... < b_k of C(b_j, j)
+    int r = 0, j = 0;
+    for (int b = 0; b < 8; ++b)
+        if (code >> b & 1) {
+            ++j;
+            int c = 1;
+            for (int i = 1; i <= j; ++i) c = c * (b - j + i) / i;
+            r += (j <= b) ? c : 0;
+        }
+    return r;
+}
+
+int ldp_num_variants(void) { return ldp::num_variants(); }
+
+const char* ldp_variant_name(int variant) { return ldp::variant_name(variant); }
+
+int ldp_set_plain_variant(int variant) {
+    if (variant < 0 || variant >= ldp::num_variants()) return fail(LDP_EINVAL, "variant out of range");
+    g_plain_variant.store(variant);
+    return LDP_OK;
+}
+
+int ldp_codes(const uint8_t* d_img, int H, int W, int pitch, int k, uint8_t* d_codes, int code_pitch,
+              void* stream) {
+    int rc;
+    if ((rc = check_image(d_img, H, W, pitch))) return rc;
+    if ((rc = check_codes(d_codes, W, code_pitch, true))) return rc;
+    if (k < 1 || k > 7) return fail(LDP_EINVAL, "k must be in [1,7]");
+    return run_plain(0, d_img, H, W, pitch, k, 1, 1, 0, nullptr, d_codes, code_pitch, stream);
+}
+
+int ldp_region_hist(const uint8_t* d_img, int H, int W, int pitch, int k, ldp_region_spec rs,
+                    uint32_t* d_hist, uint8_t* d_codes_or_null, int code_pitch, void* stream) {
+    int rc;
+    if ((rc = check_image(d_img, H, W, pitch))) return rc;
+    if ((rc = check_codes(d_codes_or_null, W, code_pitch, false))) return rc;
+    if (k < 1 || k > 7) return fail(LDP_EINVAL, "k must be in [1,7]");
+    if ((rc = check_regions(rs.R, rs.C))) return rc;
+    if (rs.compact != 0 && rs.compact != 1) return fail(LDP_EINVAL, "compact must be 0 or 1");
+    if (!d_hist) return fail(LDP_EINVAL, "histogram pointer is NULL");
+    return run_plain(0, d_img, H, W, pitch, k, rs.R, rs.C, rs.compact, d_hist, d_codes_or_null, code_pitch,
+                     stream);
+}
+
+int lbp_codes(const uint8_t* d_img, int H, int W, int pitch, uint8_t* d_codes, int code_pitch, void* stream) {
+    int rc;
+    if ((rc = check_image(d_img, H, W, pitch))) return rc;
+    if ((rc = check_codes(d_codes, W, code_pitch, true))) return rc;
+    return run_plain(1, d_img, H, W, pitch, 1, 1, 1, 0, nullptr, d_codes, code_pitch, stream);
+}
+
+int lbp_region_hist(const uint8_t* d_img, int H, int W, int pitch, int R, int C, uint32_t* d_hist,
+                    uint8_t* d_codes_or_null, int code_pitch, void* stream) {
+    int rc;
+    if ((rc = check_image(d_img, H, W, pitch))) return rc;
+    if ((rc = check_codes(d_codes_or_null, W, code_pitch, false))) return rc;
+    if ((rc = check_regions(R, C))) return rc;
+    if (!d_hist) return fail(LDP_EINVAL, "histogram pointer is NULL");
+    return run_plain(1, d_img, H, W, pitch, 1, R, C, 0, d_hist, d_codes_or_null, code_pitch, stream);
+}
+
+int ldp_batch_plan_create(ldp_batch_plan** out, int max_images, uint64_t max_pixels, int k, ldp_region_spec rs,
+                          unsigned flags) {
+    if (!out) return fail(LDP_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (max_images < 1 || max_images > (1 << 24)) return fail(LDP_EINVAL, "max_images must be in [1, 1<<24]");
+    if (max_pixels < 9) return fail(LDP_EINVAL, "max_pixels must be at least 9");
+    const int mode = (flags & LDP_PLAN_LBP) ? 1 : 0;
+    if (mode == 0 && (k < 1 || k > 7)) return fail(LDP_EINVAL, "k must be in [1,7]");
+    int rc;
+    if ((rc = check_regions(rs.R, rs.C))) return rc;
+    if (rs.compact != 0 && rs.compact != 1) return fail(LDP_EINVAL, "compact must be 0 or 1");
+    // Tiles of an image: ceil((H-2)/TH)*ceil((W-2)/128) <= HW/(TH*128) + (H+W)/min(TH,128) + 1,
+    // and H + W <= 2HW/3 for H, W >= 3; every variant has TH >= 64.
+    const double bound = (double)max_pixels / (64.0 * 128.0) + (2.0 / 3.0) * (double)max_pixels / 64.0 +
+                         (double)max_images + 1.0;
+    if (bound > 1.5e9) return fail(LDP_EINVAL, "max_pixels too large for one plan");
+    ldp_batch_plan* p = new (std::nothrow) ldp_batch_plan();
+    if (!p) return fail(LDP_ENOMEM, "host allocation failed");
+    p->mode = mode;
+    p->k = mode == 0 ? k : 1;
+    p->rs = rs;
+    if (mode == 1) p->rs.compact = 0;
+    p->flags = flags;
+    p->max_images = max_images;
+    p->max_pixels = max_pixels;
+    p->max_tiles = (int)bound;
+    cudaError_t e = cudaGetDevice(&p->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device);
+    if (e != cudaSuccess) {
+        delete p;
+        return cuda_fail(e, "querying the device");
+    }
+    const size_t n_ints = (size_t)(max_images + 1) + (size_t)p->max_tiles + 2;
+    e = cudaMalloc(&p->scratch, n_ints * sizeof(int));
+    if (e != cudaSuccess) {
+        delete p;
+        cudaGetLastError();
+        return fail(LDP_ENOMEM, "device allocation of the plan's work list failed");
+    }
+    int* base = static_cast<int*>(p->scratch);
+    p->scr.counter = base;
+    p->scr.total = base + 1;
+    p->scr.prefix = base + 2;
+    p->scr.tile_img = base + 2 + (max_images + 1);
+    *out = p;
+    return LDP_OK;
+}
+
+int ldp_batch_plan_set_config(ldp_batch_plan* plan, int variant, int ctas_per_sm) {
+    if (!plan) return fail(LDP_EINVAL, "plan is NULL");
+    if (variant < 0 || variant >= ldp::num_variants()) return fail(LDP_EINVAL, "variant out of range");
+    if (ctas_per_sm < 0 || ctas_per_sm > 64) return fail(LDP_EINVAL, "ctas_per_sm out of range");
+    plan->variant = variant;
+    plan->ctas_per_sm = ctas_per_sm;
+    return LDP_OK;
+}
+
+static int batch_run(ldp_batch_plan* plan, int mode, const ldp_image_desc* d_descs, const int* d_count,
+                     uint32_t* d_hist, void* stream) {
+    if (!plan) return fail(LDP_EINVAL, "plan is NULL");
+    if (plan->mode != mode) return fail(LDP_EINVAL, "plan was created for the other descriptor (LDP vs LBP)");
+    if (!d_descs || !d_count) return fail(LDP_EINVAL, "descriptor or count pointer is NULL");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    ldp::BatchArgs a{};
+    a.descs = d_descs;
+    a.count = d_count;
+    a.hist = d_hist;
+    a.max_images = plan->max_images;
+    a.max_tiles = plan->max_tiles;
+    a.scr = plan->scr;
+    a.hc.R = plan->rs.R;
+    a.hc.C = plan->rs.C;
+    a.hc.compact = (mode == 0 && plan->rs.compact) ? 1 : 0;
+    a.hc.nbins = a.hc.compact ? binom8(plan->k) : 256;
+    int occ = 0;
+    cudaError_t e = ldp::batch_occupancy(mode, plan->k, d_hist != nullptr, plan->variant, &occ);
+    if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
+    if (occ < 1) return fail(LDP_ENOTIMPL, "persistent kernel does not fit on an SM");
+    const int per_sm = plan->ctas_per_sm > 0 ? (plan->ctas_per_sm < occ ? plan->ctas_per_sm : occ) : occ;
+    const int grid = plan->num_sms * per_sm;
+    const bool hist = d_hist != nullptr;
+    const bool timed = plan->nrec < (int)plan->ev_start.size();
+    if (!plan->ph_start) {
+        e = cudaEventCreate(&plan->ph_start);
+        if (e == cudaSuccess) e = cudaEventCreate(&plan->ph_end);
+        if (e != cudaSuccess) return cuda_fail(e, "creating timing events");
+    }
+    if (plan->flags & LDP_PLAN_NO_GRAPH) {
+        e = ldp::launch_batch_prep(plan->variant, a, s);
+        if (e != cudaSuccess) return cuda_fail(e, "batch preparation launch");
+        if (timed) cudaEventRecord(plan->ev_start[plan->nrec], s);
+        e = ldp::launch_batch_main(mode, plan->k, hist, plan->variant, grid, a, s);
+        if (e != cudaSuccess) return cuda_fail(e, "persistent kernel launch");
+        if (timed) {
+            e = cudaEventRecord(plan->ev_end[plan->nrec], s);
+            if (e != cudaSuccess) return cuda_fail(e, "recording a timing event");
+            ++plan->nrec;
+        }
+        return LDP_OK;
+    }
+    if (!plan->exec || plan->g_descs != d_descs || plan->g_count != d_count || plan->g_hist != d_hist ||
+        plan->g_variant != plan->variant || plan->g_grid != grid) {
+        if (plan->exec) {
+            cudaGraphExecDestroy(plan->exec);
+            plan->exec = nullptr;
+        }
+        if (plan->graph) {
+            cudaGraphDestroy(plan->graph);
+            plan->graph = nullptr;
+        }
+        if (!plan->cap_stream) {
+            e = cudaStreamCreateWithFlags(&plan->cap_stream, cudaStreamNonBlocking);
+            if (e != cudaSuccess) return cuda_fail(e, "creating the capture stream");
+        }
+        cudaGraph_t g = nullptr;
+        e = cudaStreamBeginCapture(plan->cap_stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_fail(e, "beginning graph capture");
+        cudaError_t e1 = ldp::launch_batch_prep(plan->variant, a, plan->cap_stream);
+        // external event records become event-record nodes of the captured graph
+        if (e1 == cudaSuccess) e1 = cudaEventRecordWithFlags(plan->ph_start, plan->cap_stream, cudaEventRecordExternal);
+        cudaError_t e2 = e1 == cudaSuccess
+                             ? ldp::launch_batch_main(mode, plan->k, hist, plan->variant, grid, a, plan->cap_stream)
+                             : e1;
+        if (e2 == cudaSuccess) e2 = cudaEventRecordWithFlags(plan->ph_end, plan->cap_stream, cudaEventRecordExternal);
+        e = cudaStreamEndCapture(plan->cap_stream, &g);
+        if (e2 != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return cuda_fail(e2, "capturing the batch launches");
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "ending graph capture");
+        // find the two event-record nodes (start / end of the persistent kernel)
+        plan->node_start = plan->node_end = nullptr;
+        size_t nn = 0;
+        cudaGraphGetNodes(g, nullptr, &nn);
+        std::vector<cudaGraphNode_t> nodes(nn);
+        if (nn) cudaGraphGetNodes(g, nodes.data(), &nn);
+        for (cudaGraphNode_t nd : nodes) {
+            cudaGraphNodeType ty;
+            if (cudaGraphNodeGetType(nd, &ty) != cudaSuccess || ty != cudaGraphNodeTypeEventRecord) continue;
+            cudaEvent_t ev = nullptr;
+            cudaGraphEventRecordNodeGetEvent(nd, &ev);
+            if (ev == plan->ph_start) plan->node_start = nd;
+            if (ev == plan->ph_end) plan->node_end = nd;
+        }
+        e = cudaGraphInstantiate(&plan->exec, g, 0);
+        if (e != cudaSuccess) {
+            cudaGraphDestroy(g);
+            plan->exec = nullptr;
+            return cuda_fail(e, "instantiating the batch graph");
+        }
+        plan->graph = g;
+        if (!plan->node_start || !plan->node_end) return fail(LDP_ECUDA, "timing nodes missing from the graph");
+        plan->g_descs = d_descs;
+        plan->g_count = d_count;
+        plan->g_hist = d_hist;
+        plan->g_variant = plan->variant;
+        plan->g_grid = grid;
+    }
+    cudaEvent_t es = timed ? plan->ev_start[plan->nrec] : plan->ph_start;
+    cudaEvent_t ee = timed ? plan->ev_end[plan->nrec] : plan->ph_end;
+    e = cudaGraphExecEventRecordNodeSetEvent(plan->exec, plan->node_start, es);
+    if (e == cudaSuccess) e = cudaGraphExecEventRecordNodeSetEvent(plan->exec, plan->node_end, ee);
+    if (e != cudaSuccess) return cuda_fail(e, "setting the graph's timing events");
+    e = cudaGraphLaunch(plan->exec, s);
+    if (e != cudaSuccess) return cuda_fail(e, "graph launch");
+    if (timed) ++plan->nrec;
+    return LDP_OK;
+}
+
+int ldp_batch_plan_enable_timing(ldp_batch_plan* plan, int capacity) {
+    if (!plan) return fail(LDP_EINVAL, "plan is NULL");
+    if (capacity < 0 || capacity > (1 << 20)) return fail(LDP_EINVAL, "capacity out of range");
+    while ((int)plan->ev_start.size() < capacity) {
+        cudaEvent_t a = nullptr, b = nullptr;
+        cudaError_t e = cudaEventCreate(&a);
+        if (e == cudaSuccess) e = cudaEventCreate(&b);
+        if (e != cudaSuccess) {
+            if (a) cudaEventDestroy(a);
+            return cuda_fail(e, "creating timing events");
+        }
+        plan->ev_start.push_back(a);
+        plan->ev_end.push_back(b);
+    }
+    plan->nrec = 0;
+    return LDP_OK;
+}
+
+int ldp_batch_plan_kernel_times(ldp_batch_plan* plan, float* ms, int capacity, int* count) {
+    if (!plan || !count || (capacity > 0 && !ms)) return fail(LDP_EINVAL, "NULL argument");
+    const int n = plan->nrec < capacity ? plan->nrec : capacity;
+    for (int i = 0; i < n; ++i) {
+        cudaError_t e = cudaEventSynchronize(plan->ev_end[i]);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms[i], plan->ev_start[i], plan->ev_end[i]);
+        if (e != cudaSuccess) return cuda_fail(e, "reading timing events");
+    }
+    *count = n;
+    plan->nrec = 0;
+    return LDP_OK;
+}
+
+int ldp_batch_run(ldp_batch_plan* plan, const ldp_image_desc* d_descs, const int* d_count, uint32_t* d_hist,
+                  void* stream) {
+    return batch_run(plan, 0, d_descs, d_count, d_hist, stream);
+}
+
+int lbp_batch_run(ldp_batch_plan* plan, const ldp_image_desc* d_descs, const int* d_count, uint32_t* d_hist,
+                  void* stream) {
+    return batch_run(plan, 1, d_descs, d_count, d_hist, stream);
+}
+
+int ldp_batch_plan_destroy(ldp_batch_plan* plan) {
+    if (!plan) return LDP_OK;
+    cudaDeviceSynchronize();
+    if (plan->exec) cudaGraphExecDestroy(plan->exec);
+    if (plan->graph) cudaGraphDestroy(plan->graph);
+    if (plan->cap_stream) cudaStreamDestroy(plan->cap_stream);
+    for (cudaEvent_t ev : plan->ev_start) cudaEventDestroy(ev);
+    for (cudaEvent_t ev : plan->ev_end) cudaEventDestroy(ev);
+    if (plan->ph_start) cudaEventDestroy(plan->ph_start);
+    if (plan->ph_end) cudaEventDestroy(plan->ph_end);
+    if (plan->scratch) cudaFree(plan->scratch);
+    delete plan;
+    return LDP_OK;
+}
+
+int ldp_device_status(void* stream, int* out) {
+    if (!out) return fail(LDP_EINVAL, "out is NULL");
+    cudaError_t e = ldp::read_clear_status(static_cast<cudaStream_t>(stream), out);
+    if (e != cudaSuccess) return cuda_fail(e, "reading the device status");
+    return LDP_OK;
+}
+
+}  // extern "C"

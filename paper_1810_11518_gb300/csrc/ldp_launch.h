@@ -1,0 +1,74 @@
+// Internal interface between the C-ABI layer (ldp_abi.cu) and the kernel
+// translation unit (ldp_kernels.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "../../include/ldp.h"
+
+namespace ldp {
+
+struct JobArgs {
+    const uint8_t* img;
+    int H, W, P;
+    uint8_t* codes;
+    int Pc;
+    uint32_t* hist;
+};
+
+struct HistArgs {
+    int R, C, nbins, compact;
+};
+
+// Device scratch of a batch plan (owned by the plan).
+struct BatchScratch {
+    int* prefix;    // [max_images + 1] exclusive scan of tiles per image
+    int* tile_img;  // [max_tiles] image of each tile
+    int* counter;   // next tile to hand out
+    int* total;     // tiles of this run
+};
+
+struct BatchArgs {
+    const ldp_image_desc* descs;
+    const int* count;
+    uint32_t* hist;
+    int max_images;
+    int max_tiles;
+    BatchScratch scr;
+    HistArgs hc;
+};
+
+// Tile variants X(id, rows per warp, warps): tile = 128 columns x rows*warps.
+// ldp_kernels.cu is compiled once per entry (the build script reads this list).
+#define LDP_VARIANTS(X) X(0, 16, 4) X(1, 16, 8) X(2, 8, 8) X(3, 32, 4)
+
+#define LDP_DECLARE_VARIANT(ID, RPW, NW)                                                                  \
+    namespace var##ID {                                                                                   \
+    cudaError_t launch_plain(int mode, int k, bool hist, const JobArgs& jb, const HistArgs& hc,           \
+                             cudaStream_t s);                                                             \
+    cudaError_t launch_batch_main(int mode, int k, bool hist, int grid, const BatchArgs& a, cudaStream_t s); \
+    cudaError_t batch_occupancy(int mode, int k, bool hist, int* blocks_per_sm);                          \
+    }
+LDP_VARIANTS(LDP_DECLARE_VARIANT)
+#undef LDP_DECLARE_VARIANT
+
+int num_variants();
+const char* variant_name(int v);
+int variant_tile_h(int v);
+
+// mode: 0 = LDP, 1 = LBP.  hist = fused region histograms.
+cudaError_t launch_plain(int mode, int k, bool hist, int variant, const JobArgs& jb, const HistArgs& hc,
+                         cudaStream_t s);
+
+// Prep (scan + tile map + histogram zeroing) and the persistent kernel.
+cudaError_t launch_batch_prep(int variant, const BatchArgs& a, cudaStream_t s);
+cudaError_t launch_batch_main(int mode, int k, bool hist, int variant, int grid, const BatchArgs& a,
+                              cudaStream_t s);
+// Resident CTAs per SM of the persistent kernel.
+cudaError_t batch_occupancy(int mode, int k, bool hist, int variant, int* blocks_per_sm);
+
+cudaError_t read_clear_status(cudaStream_t s, int* out);
+
+}  // namespace ldp

@@ -1,0 +1,103 @@
+"""The C-ABI library on a machine without a GPU: it builds, loads, exports
+every function include/ldp.h declares, and rejects bad arguments on the host
+before any CUDA call.  No compute call is made here."""
+import ctypes
+import os
+import re
+from math import comb
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1810_11518_gb300 import _abi
+    from paper_1810_11518_gb300 import build as libbuild
+
+    libbuild.build()
+    return _abi.load()
+
+
+def _declared():
+    with open(os.path.join(ROOT, "include", "ldp.h")) as f:
+        src = f.read()
+    return re.findall(r"LDP_API\s+(?:int|const char \*)\s*(\w+)\(", src)
+
+
+def test_exports_every_declared_symbol(lib):
+    from paper_1810_11518_gb300 import _abi
+
+    names = _declared()
+    assert len(names) >= 17
+    assert sorted(names) == sorted(_abi.EXPORTS)
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_variants_listed(lib):
+    from paper_1810_11518_gb300 import build as libbuild
+
+    nv = lib.ldp_num_variants()
+    assert nv == len(libbuild.variants()) and nv >= 1
+    for v in range(nv):
+        name = lib.ldp_variant_name(v).decode()
+        assert re.fullmatch(r"r\d+w\d+", name)
+    assert lib.ldp_variant_name(nv) == b""
+    assert lib.ldp_set_plain_variant(nv) == 1
+
+
+def test_host_helpers(lib):
+    import oracle
+
+    for k in range(0, 9):
+        assert lib.ldp_hist_bins(k) == comb(8, k)
+    assert lib.ldp_hist_bins(9) == -1
+    for k in range(1, 8):
+        for code in range(256):
+            assert lib.ldp_bin_of_code(code, k) == oracle.bin_of_code(code, k)
+    assert lib.ldp_version() >= 100
+
+
+def test_argument_errors_without_gpu(lib):
+    from paper_1810_11518_gb300 import _abi
+
+    fake = ctypes.c_void_p(0x1000)
+    rs = _abi.RegionSpec(7, 6, 1)
+    EINVAL = _abi.LDP_EINVAL
+    assert lib.ldp_codes(None, 10, 10, 10, 3, fake, 8, None) == EINVAL
+    assert lib.ldp_codes(fake, 2, 10, 10, 3, fake, 8, None) == EINVAL
+    assert lib.ldp_codes(fake, 10, 2, 10, 3, fake, 8, None) == EINVAL
+    assert lib.ldp_codes(fake, 10, 10, 9, 3, fake, 8, None) == EINVAL
+    assert lib.ldp_codes(fake, 10, 10, 10, 3, fake, 7, None) == EINVAL
+    assert lib.ldp_codes(fake, 10, 10, 10, 0, fake, 8, None) == EINVAL
+    assert lib.ldp_codes(fake, 10, 10, 10, 8, fake, 8, None) == EINVAL
+    assert lib.ldp_codes(fake, 10, 10, 10, 3, None, 8, None) == EINVAL
+    assert lib.ldp_codes(fake, (1 << 20) + 1, 10, 10, 3, fake, 8, None) == EINVAL
+    assert b"pitch" in lib.ldp_last_error() or lib.ldp_last_error()
+    assert lib.ldp_region_hist(fake, 10, 10, 10, 3, _abi.RegionSpec(0, 6, 1), fake, None, 0, None) == EINVAL
+    assert lib.ldp_region_hist(fake, 10, 10, 10, 3, _abi.RegionSpec(7, 6, 2), fake, None, 0, None) == EINVAL
+    assert lib.ldp_region_hist(fake, 10, 10, 10, 3, rs, None, None, 0, None) == EINVAL
+    assert lib.lbp_codes(fake, 10, 10, 10, None, 8, None) == EINVAL
+    assert lib.lbp_region_hist(fake, 10, 10, 10, 0, 1, fake, None, 0, None) == EINVAL
+    h = ctypes.c_void_p()
+    assert lib.ldp_batch_plan_create(None, 4, 1000, 3, rs, 0) == EINVAL
+    assert lib.ldp_batch_plan_create(ctypes.byref(h), 0, 1000, 3, rs, 0) == EINVAL
+    assert lib.ldp_batch_plan_create(ctypes.byref(h), 4, 1000, 9, rs, 0) == EINVAL
+    assert lib.ldp_batch_run(None, fake, fake, fake, None) == EINVAL
+    assert lib.ldp_batch_plan_destroy(None) == 0
+    out = ctypes.c_int()
+    assert lib.ldp_device_status(None, None) == EINVAL
+
+
+def test_layout_alignment():
+    import paper_1810_11518_gb300 as ldp
+
+    lay = ldp.BatchLayout.build([3, 100, 490], [3, 77, 640], hist_len=2352)
+    assert (lay.pitches % 16 == 0).all() and (lay.img_off % 16 == 0).all()
+    assert (lay.code_pitches % 16 == 0).all() and (lay.code_off % 16 == 0).all()
+    assert (lay.pitches >= lay.Ws).all() and (lay.code_pitches >= lay.Ws - 2).all()
+    d = lay.descs(1 << 20, 1 << 30)
+    assert d["hist_offset"].tolist() == [0, 2352, 4704]
+    assert d.itemsize == 40
