@@ -165,6 +165,38 @@ LDP_API const char *ldp_variant_name(int variant);
 /* Variant used by the single-image entry points (default 0). */
 LDP_API int ldp_set_plain_variant(int variant);
 
+/* Batch run that allocates nothing, for callers that cannot call
+ * cudaMalloc / cudaFree while they run (device memory budgeted once at
+ * start-up, memory owned by another allocator's pool, or loops that must
+ * not risk an allocation failure or the device-wide synchronisation
+ * cudaFree can cause).  The paper has no counterpart: it is a deployment
+ * variant of ldp_batch_run.
+ *
+ * Same work as an LDP plan run (codes when desc.codes != NULL, region
+ * histograms zeroed and accumulated in d_hist when d_hist != NULL), but:
+ *   - count (number of descriptors in d_descs) is a host value;
+ *   - no plan and no CUDA graph: four direct kernel launches on `stream`;
+ *   - the work list lives in one static device array of 2^21 ints (8 MiB)
+ *     that every GPU loading the library keeps until the process exits.
+ *     The caller bounds the batch by max_pixels (sum of H*W) and max_side
+ *     (largest H or W); the call returns LDP_EINVAL, with the sizes in
+ *     ldp_last_error(), when
+ *       3 + (count+1) + max_pixels/8192 + 1 + count*(max_side/64 + max_side/128 + 3)
+ *     exceeds 2^21.  (4096 images of 640x490 fit with room to spare.)
+ *     A batch that breaks its own bounds is clamped on the device and
+ *     flagged in the device status word (bit 1).
+ *   - the first call on each device looks up the array's address
+ *     (cudaGetSymbolAddress) with that device current: make it before any
+ *     stream capture.
+ *   - every call shares the array, which keeps the last call's contents;
+ *     each call rewrites what it reads first.  Calls that overlap on the GPU
+ *     (other streams or host threads) race on it: serialise them.
+ * EINVAL also for count < 0, NULL d_descs with count > 0, bad k or rs,
+ * max_side outside [3, 1<<20]. */
+LDP_API int ldp_batch_run_noalloc(const ldp_image_desc *d_descs, int count, uint64_t max_pixels,
+                                  int max_side, int k, ldp_region_spec rs, uint32_t *d_hist,
+                                  void *stream);
+
 /* ---- helpers ---- */
 
 /* Compact bins for k (Eq. 6): C(8,k), or -1 when k is outside [0,8]. */

@@ -22,7 +22,7 @@ from ._abi import LdpError, RegionSpec
 
 __all__ = ["codes", "region_hist", "lbp_codes", "lbp_region_hist", "hist_bins", "bin_of_code",
            "BatchPlan", "BatchLayout", "DESC_DTYPE", "LdpError", "device_status", "num_variants",
-           "variant_name", "set_plain_variant", "load"]
+           "variant_name", "set_plain_variant", "load", "batch_run_noalloc"]
 
 DESC_DTYPE = np.dtype([("img", "<u8"), ("H", "<i4"), ("W", "<i4"), ("pitch", "<i4"),
                        ("code_pitch", "<i4"), ("codes", "<u8"), ("hist_offset", "<u8")])
@@ -146,6 +146,17 @@ def device_status(stream=None) -> int:
     out = ctypes.c_int(0)
     _abi.call("ldp_device_status", _stream(stream), ctypes.byref(out))
     return out.value
+
+
+def batch_run_noalloc(d_descs, count: int, max_pixels: int, max_side: int, d_hist, k: int = 3,
+                      regions=(7, 6), compact: bool = True, stream=None) -> None:
+    """Batched LDP run that allocates no device memory (static work list of
+    2^21 ints shared by all calls; see ldp_batch_run_noalloc in ldp.h).
+    For callers that budget device memory once and cannot allocate per batch.
+    Calls must not overlap on the GPU."""
+    hist_ptr = ctypes.c_void_p(d_hist.data_ptr()) if d_hist is not None else None
+    _abi.call("ldp_batch_run_noalloc", ctypes.c_void_p(d_descs.data_ptr()), int(count), int(max_pixels),
+              int(max_side), int(k), RegionSpec(regions[0], regions[1], int(compact)), hist_ptr, _stream(stream))
 
 
 @dataclass

@@ -25,7 +25,7 @@ EXPORTS = [
     "ldp_batch_plan_create", "ldp_batch_run", "lbp_batch_run", "ldp_batch_plan_destroy",
     "ldp_batch_plan_set_config", "ldp_num_variants", "ldp_variant_name", "ldp_set_plain_variant",
     "ldp_hist_bins", "ldp_bin_of_code", "ldp_last_error", "ldp_device_status", "ldp_version",
-    "ldp_batch_plan_enable_timing", "ldp_batch_plan_kernel_times",
+    "ldp_batch_plan_enable_timing", "ldp_batch_plan_kernel_times", "ldp_batch_run_noalloc",
 ]
 
 
@@ -83,6 +83,7 @@ def load(path: str | None = None):
             "ldp_version": [],
             "ldp_batch_plan_enable_timing": [vp, i32],
             "ldp_batch_plan_kernel_times": [vp, ctypes.POINTER(ctypes.c_float), i32, ctypes.POINTER(i32)],
+            "ldp_batch_run_noalloc": [vp, i32, u64, i32, i32, RegionSpec, vp, vp],
         }
         for name, args in sig.items():
             fn = getattr(lib, name)

@@ -72,6 +72,11 @@ int run_plain(int mode, const uint8_t* img, int H, int W, int pitch, int k, int 
 
 }  // namespace
 
+namespace ldp {
+// Records msg as the calling thread's ldp_last_error() text.
+int report_error(int code, const char* msg) { return fail(code, msg); }
+}  // namespace ldp
+
 struct ldp_batch_plan {
     int mode = 0, k = 3;
     ldp_region_spec rs{1, 1, 0};
