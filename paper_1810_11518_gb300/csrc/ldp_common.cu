@@ -12,9 +12,9 @@ namespace ldp {
 // bit 1 = a batch needed more tiles than its plan holds.
 __device__ int g_status;
 
-#define LDP_NAME(ID, RPW, NW) "r" #RPW "w" #NW,
-#define LDP_TH(ID, RPW, NW) (RPW) * (NW),
-#define LDP_COUNT(ID, RPW, NW) +1
+#define LDP_NAME(ID, RPW, NW, MB) "r" #RPW "w" #NW "b" #MB,
+#define LDP_TH(ID, RPW, NW, MB) (RPW) * (NW),
+#define LDP_COUNT(ID, RPW, NW, MB) +1
 static const char* kVariantNames[] = {LDP_VARIANTS(LDP_NAME)};
 static const int kVariantTH[] = {LDP_VARIANTS(LDP_TH)};
 constexpr int kNumVariants = 0 LDP_VARIANTS(LDP_COUNT);
@@ -117,7 +117,7 @@ cudaError_t launch_batch_prep(int variant, const BatchArgs& a, cudaStream_t s) {
 cudaError_t launch_plain(int mode, int k, bool hist, int variant, const JobArgs& jb, const HistArgs& hc,
                          cudaStream_t s) {
     switch (variant) {
-#define LDP_CASE(ID, RPW, NW) \
+#define LDP_CASE(ID, RPW, NW, MB) \
     case ID: return var##ID::launch_plain(mode, k, hist, jb, hc, s);
         LDP_VARIANTS(LDP_CASE)
 #undef LDP_CASE
@@ -128,7 +128,7 @@ cudaError_t launch_plain(int mode, int k, bool hist, int variant, const JobArgs&
 cudaError_t launch_batch_main(int mode, int k, bool hist, int variant, int grid, const BatchArgs& a,
                               cudaStream_t s) {
     switch (variant) {
-#define LDP_CASE(ID, RPW, NW) \
+#define LDP_CASE(ID, RPW, NW, MB) \
     case ID: return var##ID::launch_batch_main(mode, k, hist, grid, a, s);
         LDP_VARIANTS(LDP_CASE)
 #undef LDP_CASE
@@ -138,7 +138,7 @@ cudaError_t launch_batch_main(int mode, int k, bool hist, int variant, int grid,
 
 cudaError_t batch_occupancy(int mode, int k, bool hist, int variant, int* blocks_per_sm) {
     switch (variant) {
-#define LDP_CASE(ID, RPW, NW) \
+#define LDP_CASE(ID, RPW, NW, MB) \
     case ID: return var##ID::batch_occupancy(mode, k, hist, blocks_per_sm);
         LDP_VARIANTS(LDP_CASE)
 #undef LDP_CASE

@@ -4,14 +4,18 @@
 // consecutive ring neighbours by 5 and the other five by -3, so
 //     m_i = 8*S3_i - 3*S8,   S3_i = p_{i-1} + p_i + p_{i+1},  S8 = sum_j p_j
 // (ring p_0..p_7 counter-clockwise from East).  The eight S3_i and S8 are
-// built from column and row three-sums shared between neighbouring pixels.
+// built from column and row sums shared between neighbouring pixels.
 //
-// Ranking: with D_i = 256*m_i = 2048*S3_i - 768*S8 (low 8 bits zero) the key
-//     key_i = 2^20 - |D_i| + 2^i
-// is unique per direction, orders by |m_i| descending, and breaks ties toward
-// the lower index (smaller 2^i).  The k smallest keys are the k most
-// outstanding responses, and because the low bytes of the keys are distinct
-// one-hot bits, the low byte of the sum of the k winners IS the LDP code.
+// LDP arithmetic runs in FP32 on the FMA pipe and is exact: pixels enter as
+// 2048*b (b a byte), every sum is a multiple of 2048 below 2^23, and
+//     D_i = 2048*S3_i - 0.375*(2048*S8) = 256*m_i
+// is an integer multiple of 256 with |D_i| <= 979200.  The key
+//     key_i = (2^23 + 2^20 + 2^i) - |D_i|         (one FADD, |.| folded)
+// is an integer in [2^23, 2^24), so its float bit pattern is
+// 0x4B000000 + (2^20 + 2^i - |D_i|): bit patterns order like |m_i|
+// descending, ties go to the lower index (smaller 2^i), and the low byte is
+// the one-hot bit 2^i.  The k smallest keys are the k most outstanding
+// responses, and the low byte of the sum of their bit patterns IS the code.
 #pragma once
 
 #include <cstdint>
@@ -43,11 +47,17 @@ __device__ __forceinline__ void cswap(uint32_t& a, uint32_t& b) {
     b = hi;
 }
 
-// Sum of the K smallest of eight distinct keys.
-template <int K>
-__device__ __forceinline__ uint32_t sum_k_smallest(uint32_t (&k)[8]) {
-    if constexpr (K == 3) {
-        // pairs -> sorted lowest three of each half -> bitonic half-cleaner
+// Sum of the M smallest (SMALL) or M largest of eight distinct keys.
+template <int M, bool SMALL>
+__device__ __forceinline__ uint32_t sum_extreme(uint32_t (&k)[8]) {
+    if constexpr (!SMALL) {
+        // the M largest of k are the M smallest of ~k; ~(~a) = a restores them
+#pragma unroll
+        for (int i = 0; i < 8; ++i) k[i] = ~k[i];
+    }
+    uint32_t s;
+    if constexpr (M == 3) {
+        // sorted pairs -> three smallest of each half, sorted -> bitonic half-cleaner
         cswap(k[0], k[1]);
         cswap(k[2], k[3]);
         cswap(k[4], k[5]);
@@ -56,7 +66,12 @@ __device__ __forceinline__ uint32_t sum_k_smallest(uint32_t (&k)[8]) {
         uint32_t e1 = min(ex, ey), e2 = max(ex, ey);
         uint32_t f0 = min(k[4], k[6]), fx = max(k[4], k[6]), fy = min(k[5], k[7]);
         uint32_t f1 = min(fx, fy), f2 = max(fx, fy);
-        return min(e0, f2) + min(e1, f1) + min(e2, f0);
+        uint32_t w0 = min(e0, f2), w1 = min(e1, f1), w2 = min(e2, f0);
+        s = SMALL ? w0 + w1 + w2 : (~w0) + (~w1) + (~w2);
+    } else if constexpr (M == 1) {
+        uint32_t a = min(min(k[0], k[1]), min(k[2], k[3]));
+        uint32_t b = min(min(k[4], k[5]), min(k[6], k[7]));
+        s = SMALL ? min(a, b) : ~min(a, b);
     } else {
         // Batcher odd-even merge sort of 8; unused comparator halves are
         // removed by the compiler.
@@ -66,115 +81,234 @@ __device__ __forceinline__ uint32_t sum_k_smallest(uint32_t (&k)[8]) {
         cswap(k[0], k[4]); cswap(k[1], k[5]); cswap(k[2], k[6]); cswap(k[3], k[7]);
         cswap(k[2], k[4]); cswap(k[3], k[5]);
         cswap(k[1], k[2]); cswap(k[3], k[4]); cswap(k[5], k[6]);
-        uint32_t s = 0;
+        s = 0;
 #pragma unroll
-        for (int i = 0; i < K; ++i) s += k[i];
-        return s;
+        for (int i = 0; i < M; ++i) s += SMALL ? k[i] : ~k[i];
     }
+    return s;
 }
 
-// LDP code of one pixel from its three-sums (Eq. 1-3).
+// LDP code from the eight keys: the k smallest keys win (for k >= 5 the
+// 8-k largest lose, which is the shorter network).
 template <int K>
-__device__ __forceinline__ uint32_t ldp_code(const int (&s3)[8], int s8) {
-    const int nb = s8 * -768;
-    uint32_t key[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) key[i] = (kKeyBase + (1u << i)) - (uint32_t)abs(s3[i] * 2048 + nb);
-    return sum_k_smallest<K>(key) & 0xFFu;
-}
-
-// Bytes at columns v..v+5 of one image row as ints (zero past column W-1).
-__device__ __forceinline__ void load_row6(const uint8_t* __restrict__ row, int v, int W, bool fast,
-                                          int (&b)[6]) {
-    if (fast) {
-        uint32_t w0 = __ldg(reinterpret_cast<const unsigned int*>(row + v));
-        uint32_t w1 = __ldg(reinterpret_cast<const unsigned short*>(row + v + 4));
-#pragma unroll
-        for (int j = 0; j < 4; ++j) b[j] = (int)__byte_perm(w0, 0u, 0x4440u + j);
-        b[4] = (int)(w1 & 0xFFu);
-        b[5] = (int)(w1 >> 8);
+__device__ __forceinline__ uint32_t select_code(uint32_t (&key)[8]) {
+    if constexpr (K <= 4) {
+        return sum_extreme<K, true>(key) & 0xFFu;
     } else {
-#pragma unroll
-        for (int j = 0; j < 6; ++j) b[j] = (v + j < W) ? (int)__ldg(row + v + j) : 0;
+        return (~sum_extreme<8 - K, false>(key)) & 0xFFu;
     }
 }
 
+// One image row restricted to the six columns v..v+5 a thread needs, as
+// exact floats 2048*b, with its pair sums h2[j] = x[j] + x[j+1] and triple
+// sums hs[t] = x[t] + x[t+1] + x[t+2].
+struct FRow {
+    float x[6], h2[5], hs[4];
+};
+
+__device__ __forceinline__ float byte_x2048(uint32_t w, uint32_t j) {
+    // bits 0x4B0000bb are the float 2^23 + b; 2048*(2^23 + b) - 2^34 = 2048*b exactly
+    return __fmaf_rn(__uint_as_float(__byte_perm(w, 0x4B000000u, 0x7650u | j)), 2048.0f, -17179869184.0f);
+}
+
+// The six bytes v..v+5 of one image row a thread needs: w0 = bytes v..v+3,
+// w1 = bytes v+4, v+5 in its low half.  Columns past W-1 read as 0.
+struct Raw {
+    uint32_t w0, w1;
+};
+
+__device__ __forceinline__ Raw load_raw(const uint8_t* __restrict__ row, int v, int W, bool fast) {
+    Raw r;
+    if (fast) {
+        r.w0 = __ldg(reinterpret_cast<const unsigned int*>(row + v));
+        r.w1 = __ldg(reinterpret_cast<const unsigned short*>(row + v + 4));
+    } else {
+        uint32_t b[6];
+#pragma unroll
+        for (int j = 0; j < 6; ++j) b[j] = (v + j < W) ? (uint32_t)__ldg(row + v + j) : 0u;
+        r.w0 = b[0] | (b[1] << 8) | (b[2] << 16) | (b[3] << 24);
+        r.w1 = b[4] | (b[5] << 8);
+    }
+    return r;
+}
+
+__device__ __forceinline__ void unpack_frow(const Raw& w, FRow& r) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) r.x[j] = byte_x2048(w.w0, j);
+    r.x[4] = byte_x2048(w.w1, 0);
+    r.x[5] = byte_x2048(w.w1, 1);
+#pragma unroll
+    for (int j = 0; j < 5; ++j) r.h2[j] = r.x[j] + r.x[j + 1];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) r.hs[t] = r.h2[t] + r.x[t + 2];
+}
+
+// LBP row in byte-SIMD form: s[d] holds bytes v+d..v+d+3 (d = 0, 1, 2), i.e.
+// the row's pixel at column offset d for the four output pixels.
+struct BRow {
+    uint32_t s[3];
+};
+
+__device__ __forceinline__ void unpack_brow(const Raw& w, BRow& r) {
+    r.s[0] = w.w0;
+    r.s[1] = __byte_perm(w.w0, w.w1, 0x4321u);
+    r.s[2] = __byte_perm(w.w0, w.w1, 0x5432u);
+}
+
+// Per byte lane: bit 7 set iff x >= y (unsigned).  (x | 0x80) - (y & 0x7f)
+// never borrows across lanes and its bit 7 is [x_low7 >= y_low7]; where the
+// top bits of x and y differ, x's top bit decides instead.
+__device__ __forceinline__ uint32_t bytes_ge(uint32_t x, uint32_t y_low7) {
+    return (x | 0x80808080u) - y_low7;
+}
+
+// LBP codes of four pixels (Sec. 2.1), one per byte lane.
+__device__ __forceinline__ uint32_t lbp_row4(const BRow& A, const BRow& B, const BRow& C) {
+    const uint32_t c = B.s[1];  // centres
+    const uint32_t cl = c & 0x7F7F7F7Fu;
+    const uint32_t nb[8] = {B.s[2], A.s[2], A.s[1], A.s[0], B.s[0], C.s[0], C.s[1], C.s[2]};  // p_0..p_7
+    uint32_t acc = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {  // bit j inserted at bit 7, then shifted down 7-j times
+        const uint32_t x = nb[j];
+        const uint32_t t = bytes_ge(x, cl);
+        // bit 7 of each lane: x and c agree in bit 7 ? t : x
+        const uint32_t ge = (((x ^ c) & x) | (~(x ^ c) & t)) & 0x80808080u;
+        // shift the lanes' bits so far down by one and insert bit j at bit 7
+        acc = ((acc >> 1) & 0x7F7F7F7Fu) | ge;
+    }
+    return acc;
+}
+
+// Codes of the four pixels of one output row from rows A (x-1), B (x), C (x+1).
+template <int K>
+__device__ __forceinline__ void ldp_row4(const FRow& A, const FRow& B, const FRow& C, uint32_t (&code)[4]) {
+    float PAC[6], V[6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        PAC[j] = A.x[j] + C.x[j];  // column j: top + bottom
+        V[j] = PAC[j] + B.x[j];    // column j: vertical three-sum
+    }
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        // -0.375 * 2048*S8 = -768*S8, with S8 = V[t] + V[t+2] + A[t+1] + C[t+1]
+        const float nb = ((V[t] + V[t + 2]) + PAC[t + 1]) * -0.375f;
+        const float bn0 = B.x[t] + nb, bn2 = B.x[t + 2] + nb;
+        float D[8];
+        D[0] = V[t + 2] + nb;      // E : p7 + p0 + p1
+        D[1] = A.h2[t + 1] + bn2;  // NE: p0 + p1 + p2
+        D[2] = A.hs[t] + nb;       // N : p1 + p2 + p3
+        D[3] = A.h2[t] + bn0;      // NW: p2 + p3 + p4
+        D[4] = V[t] + nb;          // W : p3 + p4 + p5
+        D[5] = C.h2[t] + bn0;      // SW: p4 + p5 + p6
+        D[6] = C.hs[t] + nb;       // S : p5 + p6 + p7
+        D[7] = C.h2[t + 1] + bn2;  // SE: p6 + p7 + p0
+        uint32_t key[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            key[i] = __float_as_uint((8388608.0f + 1048576.0f + (float)(1 << i)) - fabsf(D[i]));
+        code[t] = select_code<K>(key);
+    }
+}
+
+// Band b of nb bands over n pixels covers [floor(b*n/nb), floor((b+1)*n/nb));
+// pixel x lies in band floor((nb*x + nb - 1) / n).
 __device__ __forceinline__ int band_of(int x, int n, int nb) {
-    // index of the band [floor(b*n/nb), floor((b+1)*n/nb)) holding x: floor((nb*x + nb - 1) / n)
     uint64_t num = (uint64_t)nb * (uint64_t)x + (uint64_t)(nb - 1);
     if (num < 0xFFFFFFFFull) return (int)((uint32_t)num / (uint32_t)n);
     return (int)(num / (uint64_t)n);
 }
 
-__device__ __forceinline__ int binom_small(int n, int r) {
-    // C(n, r) for 0 <= n < 8, computed exactly
+// Compact bin of every code, per k (Eq. 6: ascending code value among the
+// C(8,k) codes with popcount k); -1 for other popcounts.  Built at compile
+// time as the colex rank sum_j C(b_j, j) over set bits b_1 < ... < b_k.
+struct BinTable {
+    int16_t bin[9][256];
+};
+
+constexpr int binom_ce(int n, int r) {
     if (r < 0 || r > n) return 0;
     int c = 1;
     for (int i = 1; i <= r; ++i) c = c * (n - r + i) / i;
     return c;
 }
 
-// Position of a code among the codes with the same popcount, ascending:
-// its colex rank sum_j C(b_j, j) over set bits b_1 < ... < b_k.
-__device__ __forceinline__ int colex_rank(int code) {
-    int r = 0, j = 0;
-    for (int b = 0; b < 8; ++b)
-        if (code >> b & 1) {
-            ++j;
-            r += binom_small(b, j);
+constexpr BinTable make_bin_table() {
+    BinTable t{};
+    for (int k = 0; k < 9; ++k)
+        for (int code = 0; code < 256; ++code) {
+            int pop = 0, r = 0;
+            for (int b = 0; b < 8; ++b)
+                if (code >> b & 1) {
+                    ++pop;
+                    r += binom_ce(b, pop);
+                }
+            t.bin[k][code] = (int16_t)(pop == k ? r : -1);
         }
-    return r;
+    return t;
 }
 
-__device__ __forceinline__ int bin_of(int code, const HistCfg& hc) {
-    return hc.compact ? colex_rank(code) : code;
+static __device__ const BinTable g_bin_table = make_bin_table();
+
+__device__ __forceinline__ int bin_of(int code, const HistCfg& hc, int k) {
+    return hc.compact ? (int)__ldg(&g_bin_table.bin[k][code]) : code;
 }
+
+// Region slots of one tile: the R x C grid cells it touches.
+struct TileGeo {
+    int ri_lo, rj_lo, ncs, nslots, use_smem;
+};
+
+__device__ __forceinline__ TileGeo tile_geo(int H, int W, const HistCfg& hc, int u0, int v0, int TH) {
+    TileGeo g;
+    const int x_last = min(u0 + TH, H - 2), y_last = min(v0 + kTileW, W - 2);
+    g.ri_lo = band_of(u0 + 1, H, hc.R);
+    g.rj_lo = band_of(v0 + 1, W, hc.C);
+    g.ncs = band_of(y_last, W, hc.C) - g.rj_lo + 1;
+    g.nslots = (band_of(x_last, H, hc.R) - g.ri_lo + 1) * g.ncs;
+    g.use_smem = g.nslots <= kMaxSlots;
+    return g;
+}
+
+// A tile handed to the CTA: image, output origin, region slots.
+struct TileSlot {
+    Job job;
+    int u0, v0;
+    TileGeo geo;
+};
 
 // Shared memory of one CTA.
 template <int TH>
 struct Smem {
     uint32_t hist[kMaxSlots * 256];
-    int col[kTileW];  // per tile column: slot offset (smem) or rj (global)
-    int row[TH];      // per tile row: slot offset (smem) or ri*C (global)
-    int geo[8];       // ri_lo, rj_lo, ncs, nslots, use_smem
-    Job job;          // persistent kernel: current image
-    int tile_u0, tile_v0, next;
+    int col[kTileW];           // per tile column: slot offset (smem) or rj (global)
+    int row[TH];               // per tile row: slot offset (smem) or ri*C (global)
+    int slot_base[kMaxSlots];  // per slot: (ri*C + rj)*nbins in the global histogram
+    TileSlot tile[1];          // persistent kernel: the current tile
+    uint64_t stage[6];         // persistent kernel: its descriptor (40 B) + first tile index
 };
 
-// Processes one TH x 128 output tile at (u0, v0) of image `jb`.
-// All threads of the CTA must call it (it synchronises).
+// Processes one TH x 128 output tile at (u0, v0) of image `jb` whose region
+// slots are `geo`.  All threads of the CTA must call it; with HIST it
+// synchronises twice, and the caller must synchronise again before the
+// shared histogram is reused.
 template <int MODE, int K, int RPW, int NWARPS, bool HIST>
 __device__ __forceinline__ void process_tile(const Job& jb, const HistCfg& hc, int u0, int v0,
-                                             Smem<RPW * NWARPS>& sm) {
+                                             const TileGeo& geo, Smem<RPW * NWARPS>& sm) {
     constexpr int TH = RPW * NWARPS;
     constexpr int NT = NWARPS * 32;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int H = jb.H, W = jb.W;
 
-    bool use_smem = true;
+    const bool use_smem = geo.use_smem != 0;
     if constexpr (HIST) {
-        if (tid == 0) {
-            const int x_last = min(u0 + TH, H - 2), y_last = min(v0 + kTileW, W - 2);
-            const int ri_lo = band_of(u0 + 1, H, hc.R), ri_hi = band_of(x_last, H, hc.R);
-            const int rj_lo = band_of(v0 + 1, W, hc.C), rj_hi = band_of(y_last, W, hc.C);
-            const int ncs = rj_hi - rj_lo + 1, nslots = (ri_hi - ri_lo + 1) * ncs;
-            sm.geo[0] = ri_lo;
-            sm.geo[1] = rj_lo;
-            sm.geo[2] = ncs;
-            sm.geo[3] = nslots;
-            sm.geo[4] = nslots <= kMaxSlots;
-        }
-        __syncthreads();
-        const int ri_lo = sm.geo[0], rj_lo = sm.geo[1], ncs = sm.geo[2], nslots = sm.geo[3];
-        use_smem = sm.geo[4] != 0;
+        const int ri_lo = geo.ri_lo, rj_lo = geo.rj_lo, ncs = geo.ncs, nslots = geo.nslots;
         for (int j = tid; j < kTileW; j += NT) {
             const int y = v0 + 1 + j;
-            int val;
+            int val = 0;  // columns past the interior are never counted
             if (y <= W - 2) {
                 const int rj = band_of(y, W, hc.C);
                 val = use_smem ? (rj - rj_lo) * 256 : rj;
-            } else {
-                val = 0;  // column past the interior: never counted
             }
             sm.col[j] = val;
         }
@@ -187,8 +321,10 @@ __device__ __forceinline__ void process_tile(const Job& jb, const HistCfg& hc, i
             }
             sm.row[i] = val;
         }
-        if (use_smem)
+        if (use_smem) {
             for (int e = tid; e < nslots * 256; e += NT) sm.hist[e] = 0;
+            if (tid < nslots) sm.slot_base[tid] = ((ri_lo + tid / ncs) * hc.C + rj_lo + tid % ncs) * hc.nbins;
+        }
         __syncthreads();
     }
 
@@ -210,59 +346,17 @@ __device__ __forceinline__ void process_tile(const Job& jb, const HistCfg& hc, i
 #pragma unroll
             for (int t = 0; t < 4; ++t) colb[t] = sm.col[4 * lane + t];
         }
-        const uint8_t* rp = jb.img + (size_t)ub * (size_t)jb.P;
-        int A[6], B[6], Cc[6];
-        load_row6(rp, v, W, fast_ld, A);
-        load_row6(rp + jb.P, v, W, fast_ld, B);
-        // row three-sums X[t] + X[t+1] + X[t+2] of the top and middle rows
-        int hsA[4], hsB[4];
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-            hsA[t] = A[t] + A[t + 1] + A[t + 2];
-            hsB[t] = B[t] + B[t + 1] + B[t + 2];
-        }
-        rp += 2 * (size_t)jb.P;
-#pragma unroll 2
-        for (int u = ub; u < ue; ++u, rp += jb.P) {
-            load_row6(rp, v, W, fast_ld, Cc);
-            int hsC[4];
-#pragma unroll
-            for (int t = 0; t < 4; ++t) hsC[t] = Cc[t] + Cc[t + 1] + Cc[t + 2];
-            uint32_t code[4];
-            if constexpr (MODE == kLDP) {
-                int V[6];
-#pragma unroll
-                for (int j = 0; j < 6; ++j) V[j] = A[j] + B[j] + Cc[j];
-#pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    int s3[8];
-                    s3[0] = V[t + 2];
-                    s3[1] = B[t + 2] + A[t + 2] + A[t + 1];
-                    s3[2] = hsA[t];
-                    s3[3] = A[t + 1] + A[t] + B[t];
-                    s3[4] = V[t];
-                    s3[5] = B[t] + Cc[t] + Cc[t + 1];
-                    s3[6] = hsC[t];
-                    s3[7] = Cc[t + 1] + Cc[t + 2] + B[t + 2];
-                    const int s8 = V[t] + V[t + 2] + A[t + 1] + Cc[t + 1];
-                    code[t] = ldp_code<K>(s3, s8);
-                }
-            } else {
-#pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    const int c = B[t + 1];
-                    code[t] = (uint32_t)(B[t + 2] >= c) | ((uint32_t)(A[t + 2] >= c) << 1) |
-                              ((uint32_t)(A[t + 1] >= c) << 2) | ((uint32_t)(A[t] >= c) << 3) |
-                              ((uint32_t)(B[t] >= c) << 4) | ((uint32_t)(Cc[t] >= c) << 5) |
-                              ((uint32_t)(Cc[t + 1] >= c) << 6) | ((uint32_t)(Cc[t + 2] >= c) << 7);
-                }
-            }
+        const size_t P = (size_t)jb.P;
+        const uint8_t* rp = jb.img + (size_t)ub * P;
+        const uint8_t* pf = rp + 3 * P;  // next input row to prefetch (one row ahead)
+        Raw nx = load_raw(rp + 2 * P, v, W, fast_ld);
+
+        // codes of output row u -> code map and histogram
+        auto emit = [&](int u, const uint32_t (&code)[4], uint32_t packed) {
             if (jb.codes) {
                 uint8_t* cp = jb.codes + (size_t)u * (size_t)jb.Pc + v;
                 if (fast_st) {
-                    const uint32_t p01 = __byte_perm(code[0], code[1], 0x0040u);
-                    const uint32_t p23 = __byte_perm(code[2], code[3], 0x0040u);
-                    *reinterpret_cast<uint32_t*>(cp) = __byte_perm(p01, p23, 0x5410u);
+                    *reinterpret_cast<uint32_t*>(cp) = packed;
                 } else {
 #pragma unroll
                     for (int t = 0; t < 4; ++t)
@@ -279,36 +373,67 @@ __device__ __forceinline__ void process_tile(const Job& jb, const HistCfg& hc, i
 #pragma unroll
                     for (int t = 0; t < 4; ++t)
                         if (valid[t])
-                            atomicAdd(&jb.hist[(size_t)(rowb + colb[t]) * hc.nbins + bin_of((int)code[t], hc)], 1u);
+                            atomicAdd(&jb.hist[(size_t)(rowb + colb[t]) * hc.nbins + bin_of((int)code[t], hc, K)], 1u);
                 }
             }
-#pragma unroll
-            for (int j = 0; j < 6; ++j) {
-                A[j] = B[j];
-                B[j] = Cc[j];
+        };
+
+        if constexpr (MODE == kLDP) {
+            FRow r0, r1, r2;
+            unpack_frow(load_raw(rp, v, W, fast_ld), r0);
+            unpack_frow(load_raw(rp + P, v, W, fast_ld), r1);
+            auto step = [&](const FRow& A, const FRow& B, FRow& C, int u) {
+                unpack_frow(nx, C);
+                if (u + 1 < ue) nx = load_raw(pf, v, W, fast_ld);
+                pf += P;
+                uint32_t code[4];
+                ldp_row4<K>(A, B, C, code);
+                const uint32_t p01 = __byte_perm(code[0], code[1], 0x0040u);
+                const uint32_t p23 = __byte_perm(code[2], code[3], 0x0040u);
+                emit(u, code, __byte_perm(p01, p23, 0x5410u));
+            };
+            int u = ub;
+            for (; u + 3 <= ue; u += 3) {
+                step(r0, r1, r2, u);
+                step(r1, r2, r0, u + 1);
+                step(r2, r0, r1, u + 2);
             }
+            if (u < ue) step(r0, r1, r2, u);
+            if (u + 1 < ue) step(r1, r2, r0, u + 1);
+        } else {
+            BRow r0, r1, r2;
+            unpack_brow(load_raw(rp, v, W, fast_ld), r0);
+            unpack_brow(load_raw(rp + P, v, W, fast_ld), r1);
+            auto step = [&](const BRow& A, const BRow& B, BRow& C, int u) {
+                unpack_brow(nx, C);
+                if (u + 1 < ue) nx = load_raw(pf, v, W, fast_ld);
+                pf += P;
+                const uint32_t packed = lbp_row4(A, B, C);
+                uint32_t code[4];
 #pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                hsA[t] = hsB[t];
-                hsB[t] = hsC[t];
+                for (int t = 0; t < 4; ++t) code[t] = (packed >> (8 * t)) & 0xFFu;
+                emit(u, code, packed);
+            };
+            int u = ub;
+            for (; u + 3 <= ue; u += 3) {
+                step(r0, r1, r2, u);
+                step(r1, r2, r0, u + 1);
+                step(r2, r0, r1, u + 2);
             }
+            if (u < ue) step(r0, r1, r2, u);
+            if (u + 1 < ue) step(r1, r2, r0, u + 1);
         }
     }
 
     if constexpr (HIST) {
         __syncthreads();
         if (use_smem) {
-            const int ri_lo = sm.geo[0], rj_lo = sm.geo[1], ncs = sm.geo[2], nslots = sm.geo[3];
+            const int nslots = geo.nslots;
             for (int e = tid; e < nslots * 256; e += NT) {
                 const uint32_t c = sm.hist[e];
-                if (c) {
-                    const int slot = e >> 8, code = e & 255;
-                    const int ri = ri_lo + slot / ncs, rj = rj_lo + slot % ncs;
-                    atomicAdd(&jb.hist[(size_t)(ri * hc.C + rj) * hc.nbins + bin_of(code, hc)], c);
-                }
+                if (c) atomicAdd(&jb.hist[sm.slot_base[e >> 8] + bin_of(e & 255, hc, K)], c);
             }
         }
-        __syncthreads();
     }
 }
 

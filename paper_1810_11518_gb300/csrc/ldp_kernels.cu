@@ -1,5 +1,6 @@
 // Kernels of libldp for ONE tile variant (rows per warp x warps), compiled
-// once per variant with -DLDP_VAR_ID=<n> -DLDP_VAR_RPW=<rows> -DLDP_VAR_NW=<warps>:
+// once per variant with -DLDP_VAR_ID=<n> -DLDP_VAR_RPW=<rows> -DLDP_VAR_NW=<warps>
+// -DLDP_VAR_MB=<min CTAs per SM of the persistent kernel>:
 // the single-image fused kernel and the persistent batch kernel for every
 // (mode, k, histogram) combination, plus their launchers.
 #include <cuda_runtime.h>
@@ -8,7 +9,7 @@
 #include "ldp_launch.h"
 
 #ifndef LDP_VAR_ID
-#error "compile with -DLDP_VAR_ID, -DLDP_VAR_RPW and -DLDP_VAR_NW"
+#error "compile with -DLDP_VAR_ID, -DLDP_VAR_RPW, -DLDP_VAR_NW and -DLDP_VAR_MB"
 #endif
 #define LDP_CAT2(a, b) a##b
 #define LDP_CAT(a, b) LDP_CAT2(a, b)
@@ -18,7 +19,7 @@ namespace ldp {
 namespace LDP_VNS {
 
 struct VAR {
-    static constexpr int RPW = LDP_VAR_RPW, NW = LDP_VAR_NW, TH = LDP_VAR_RPW * LDP_VAR_NW;
+    static constexpr int RPW = LDP_VAR_RPW, NW = LDP_VAR_NW, TH = LDP_VAR_RPW * LDP_VAR_NW, MB = LDP_VAR_MB;
 };
 
 
@@ -45,44 +46,72 @@ __device__ __forceinline__ HistCfg to_hc(const HistArgs& h) {
 
 // ---------------- single image: one CTA per tile ----------------
 template <int MODE, int K, class V, bool HIST>
-__global__ void __launch_bounds__(V::NW * 32) k_plain(JobArgs ja, HistArgs ha) {
+__global__ void __launch_bounds__(V::NW * 32, V::MB) k_plain(JobArgs ja, HistArgs ha) {
     __shared__ Smem<V::TH> sm;
     const Job jb = to_job(ja);
-    process_tile<MODE, K, V::RPW, V::NW, HIST>(jb, to_hc(ha), blockIdx.y * V::TH, blockIdx.x * kTileW, sm);
+    const HistCfg hc = to_hc(ha);
+    const int u0 = blockIdx.y * V::TH, v0 = blockIdx.x * kTileW;
+    TileGeo geo{0, 0, 1, 1, 1};
+    if (HIST) geo = tile_geo(jb.H, jb.W, hc, u0, v0, V::TH);  // uniform: every thread computes it
+    process_tile<MODE, K, V::RPW, V::NW, HIST>(jb, hc, u0, v0, geo, sm);
 }
 
 // ---------------- persistent batch kernel ----------------
+// Asynchronous global -> shared copies.
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"((unsigned)__cvta_generic_to_shared(smem)),
+                 "l"(gmem)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"((unsigned)__cvta_generic_to_shared(smem)),
+                 "l"(gmem)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Tiles come from an atomic counter (dynamic load balance across uneven
+// images).  Thread 0 takes the next tile, copies its descriptor into shared
+// memory asynchronously and publishes it at a barrier.
 template <int MODE, int K, class V, bool HIST>
-__global__ void __launch_bounds__(V::NW * 32) k_batch(BatchArgs a) {
+__global__ void __launch_bounds__(V::NW * 32, V::MB) k_batch(BatchArgs a) {
     __shared__ Smem<V::TH> sm;
     const HistCfg hc = to_hc(a.hc);
+    const int total = *a.scr.total;
     for (;;) {
         if (threadIdx.x == 0) {
+            TileSlot& sl = sm.tile[0];
             const int t = atomicAdd(a.scr.counter, 1);
-            if (t >= *a.scr.total) {
-                sm.next = -1;
+            if (t >= total) {
+                sl.u0 = -1;
             } else {
-                const int i = a.scr.tile_img[t];
-                const int lt = t - a.scr.prefix[i];
-                const ldp_image_desc d = a.descs[i];
+                const int img = a.scr.tile_img[t];
+                const uint64_t* src = reinterpret_cast<const uint64_t*>(a.descs + img);
+#pragma unroll
+                for (int w = 0; w < 5; ++w) cp_async8(&sm.stage[w], src + w);
+                cp_async4(&sm.stage[5], a.scr.prefix + img);
+                cp_async_wait_all();
+                const ldp_image_desc& d = *reinterpret_cast<const ldp_image_desc*>(&sm.stage[0]);
+                const int lt = t - (int)(sm.stage[5] & 0xFFFFFFFFu);
                 const int ntx = (d.W - 2 + kTileW - 1) / kTileW;
-                sm.tile_u0 = (lt / ntx) * V::TH;
-                sm.tile_v0 = (lt % ntx) * kTileW;
-                sm.job.img = d.img;
-                sm.job.H = d.H;
-                sm.job.W = d.W;
-                sm.job.P = d.pitch;
-                sm.job.codes = d.codes;
-                sm.job.Pc = d.code_pitch;
-                sm.job.hist = a.hist ? a.hist + d.hist_offset : nullptr;
-                sm.next = t;
+                sl.u0 = (lt / ntx) * V::TH;
+                sl.v0 = (lt % ntx) * kTileW;
+                sl.job.img = d.img;
+                sl.job.H = d.H;
+                sl.job.W = d.W;
+                sl.job.P = d.pitch;
+                sl.job.codes = d.codes;
+                sl.job.Pc = d.code_pitch;
+                sl.job.hist = a.hist ? a.hist + d.hist_offset : nullptr;
+                if (HIST) sl.geo = tile_geo(d.H, d.W, hc, sl.u0, sl.v0, V::TH);
             }
         }
         __syncthreads();
-        if (sm.next < 0) break;
-        const Job jb = sm.job;
-        const int u0 = sm.tile_u0, v0 = sm.tile_v0;
-        process_tile<MODE, K, V::RPW, V::NW, HIST>(jb, hc, u0, v0, sm);
+        const TileSlot& cur = sm.tile[0];
+        if (cur.u0 < 0) break;
+        const Job jb = cur.job;
+        const TileGeo geo = cur.geo;
+        process_tile<MODE, K, V::RPW, V::NW, HIST>(jb, hc, cur.u0, cur.v0, geo, sm);
         __syncthreads();
     }
 }

@@ -6,7 +6,7 @@
 
 #include <cstdint>
 
-#include "../../include/ldp.h"
+#include "ldp.h"
 
 namespace ldp {
 
@@ -40,11 +40,13 @@ struct BatchArgs {
     HistArgs hc;
 };
 
-// Tile variants X(id, rows per warp, warps): tile = 128 columns x rows*warps.
+// Tile variants X(id, rows per warp, warps, min CTAs per SM): tile = 128
+// columns x rows*warps; the last field caps registers per thread.
 // ldp_kernels.cu is compiled once per entry (the build script reads this list).
-#define LDP_VARIANTS(X) X(0, 16, 4) X(1, 16, 8) X(2, 8, 8) X(3, 32, 4)
+#define LDP_VARIANTS(X) \
+    X(0, 16, 4, 6) X(1, 16, 4, 7) X(2, 16, 4, 8) X(3, 32, 4, 6) X(4, 16, 8, 3) X(5, 8, 8, 3)
 
-#define LDP_DECLARE_VARIANT(ID, RPW, NW)                                                                  \
+#define LDP_DECLARE_VARIANT(ID, RPW, NW, MB)                                                              \
     namespace var##ID {                                                                                   \
     cudaError_t launch_plain(int mode, int k, bool hist, const JobArgs& jb, const HistArgs& hc,           \
                              cudaStream_t s);                                                             \
