@@ -13,7 +13,7 @@ namespace ldp {
 __device__ int g_status;
 
 #define LDP_NAME(ID, RPW, NW, MB) "r" #RPW "w" #NW "b" #MB,
-#define LDP_TH(ID, RPW, NW, MB) (RPW) * (NW),
+#define LDP_TH(ID, RPW, NW, MB) (RPW),
 #define LDP_COUNT(ID, RPW, NW, MB) +1
 static const char* kVariantNames[] = {LDP_VARIANTS(LDP_NAME)};
 static const int kVariantTH[] = {LDP_VARIANTS(LDP_TH)};
@@ -31,7 +31,7 @@ __device__ __forceinline__ bool desc_ok(const ldp_image_desc& d) {
            d.pitch >= d.W && (d.codes == nullptr || d.code_pitch >= d.W - 2);
 }
 
-// One CTA: tiles per image (tile = TH rows x 128 columns), exclusive scan
+// One CTA: tiles per image (tile = TH rows x 128 columns, one warp each), exclusive scan
 // into prefix[0..n], total, and the tile counter reset.
 __global__ void __launch_bounds__(1024) k_batch_scan(BatchArgs a, int TH) {
     __shared__ int s_warp[32];

@@ -226,7 +226,7 @@ struct BinTable {
     int16_t bin[9][256];
 };
 
-constexpr int binom_ce(int n, int r) {
+__host__ __device__ constexpr int binom_ce(int n, int r) {
     if (r < 0 || r > n) return 0;
     int c = 1;
     for (int i = 1; i <= r; ++i) c = c * (n - r + i) / i;
@@ -250,104 +250,87 @@ constexpr BinTable make_bin_table() {
 
 static __device__ const BinTable g_bin_table = make_bin_table();
 
+// The C(8,k) codes with popcount k in ascending order (Eq. 6), per k.
+struct CodeList {
+    uint8_t code[9][70];
+};
+
+constexpr CodeList make_code_list() {
+    CodeList l{};
+    for (int k = 0; k < 9; ++k) {
+        int n = 0;
+        for (int code = 0; code < 256; ++code) {
+            int pop = 0;
+            for (int b = 0; b < 8; ++b) pop += (code >> b) & 1;
+            if (pop == k) l.code[k][n++] = (uint8_t)code;
+        }
+    }
+    return l;
+}
+
+static __device__ const CodeList g_code_list = make_code_list();
+
 __device__ __forceinline__ int bin_of(int code, const HistCfg& hc, int k) {
     return hc.compact ? (int)__ldg(&g_bin_table.bin[k][code]) : code;
 }
 
-// Region slots of one tile: the R x C grid cells it touches.
-struct TileGeo {
-    int ri_lo, rj_lo, ncs, nslots, use_smem;
-};
+constexpr int kWarpSlots = 8;  // region slots a warp tile may touch and still count in smem
 
-__device__ __forceinline__ TileGeo tile_geo(int H, int W, const HistCfg& hc, int u0, int v0, int TH) {
-    TileGeo g;
-    const int x_last = min(u0 + TH, H - 2), y_last = min(v0 + kTileW, W - 2);
-    g.ri_lo = band_of(u0 + 1, H, hc.R);
-    g.rj_lo = band_of(v0 + 1, W, hc.C);
-    g.ncs = band_of(y_last, W, hc.C) - g.rj_lo + 1;
-    g.nslots = (band_of(x_last, H, hc.R) - g.ri_lo + 1) * g.ncs;
-    g.use_smem = g.nslots <= kMaxSlots;
-    return g;
+// Lower bound of band b: floor(b*n/nb).
+__device__ __forceinline__ int band_lo(int b, int n, int nb) {
+    return (int)(((uint64_t)b * (uint64_t)n) / (uint64_t)nb);
 }
 
-// A tile handed to the CTA: image, output origin, region slots.
-struct TileSlot {
-    Job job;
-    int u0, v0;
-    TileGeo geo;
-};
-
-// Shared memory of one CTA.
-template <int TH>
-struct Smem {
-    uint32_t hist[kMaxSlots * 256];
-    int col[kTileW];           // per tile column: slot offset (smem) or rj (global)
-    int row[TH];               // per tile row: slot offset (smem) or ri*C (global)
-    int slot_base[kMaxSlots];  // per slot: (ri*C + rj)*nbins in the global histogram
-    TileSlot tile[1];          // persistent kernel: the current tile
-    uint64_t stage[6];         // persistent kernel: its descriptor (40 B) + first tile index
-};
-
-// Processes one TH x 128 output tile at (u0, v0) of image `jb` whose region
-// slots are `geo`.  All threads of the CTA must call it; with HIST it
-// synchronises twice, and the caller must synchronise again before the
-// shared histogram is reused.
-template <int MODE, int K, int RPW, int NWARPS, bool HIST>
-__device__ __forceinline__ void process_tile(const Job& jb, const HistCfg& hc, int u0, int v0,
-                                             const TileGeo& geo, Smem<RPW * NWARPS>& sm) {
-    constexpr int TH = RPW * NWARPS;
-    constexpr int NT = NWARPS * 32;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+// One warp processes one tile of RW output rows x 128 output columns at
+// (u0, v0): lane l owns columns v0+4l .. v0+4l+3 and walks down the rows.
+// With HIST the codes are counted in the warp's private shared histogram
+// `wh` (kWarpSlots x 256 raw bins, all zero on entry and on exit): the flush
+// adds every non-zero bin to the global histogram and resets it.  Region
+// grids too fine for kWarpSlots slots count straight into global memory.
+template <int MODE, int K, int RW, bool HIST>
+__device__ __forceinline__ void warp_tile(const Job& jb, const HistCfg& hc, int u0, int v0, uint32_t* wh) {
+    const int lane = threadIdx.x & 31;
     const int H = jb.H, W = jb.W;
+    const int ue = min(u0 + RW, H - 2);  // output rows [u0, ue) = image rows [u0+1, ue]
+    const int v = v0 + 4 * lane;
 
-    const bool use_smem = geo.use_smem != 0;
+    // region slots of the tile (uniform across the warp)
+    int ri_lo = 0, rj_lo = 0, ncs = 1, nslots = 1;
+    bool use_smem = true;
     if constexpr (HIST) {
-        const int ri_lo = geo.ri_lo, rj_lo = geo.rj_lo, ncs = geo.ncs, nslots = geo.nslots;
-        for (int j = tid; j < kTileW; j += NT) {
-            const int y = v0 + 1 + j;
-            int val = 0;  // columns past the interior are never counted
-            if (y <= W - 2) {
-                const int rj = band_of(y, W, hc.C);
-                val = use_smem ? (rj - rj_lo) * 256 : rj;
-            }
-            sm.col[j] = val;
-        }
-        for (int i = tid; i < TH; i += NT) {
-            const int x = u0 + 1 + i;
-            int val = 0;
-            if (x <= H - 2) {
-                const int ri = band_of(x, H, hc.R);
-                val = use_smem ? (ri - ri_lo) * ncs * 256 : ri * hc.C;
-            }
-            sm.row[i] = val;
-        }
-        if (use_smem) {
-            for (int e = tid; e < nslots * 256; e += NT) sm.hist[e] = 0;
-            if (tid < nslots) sm.slot_base[tid] = ((ri_lo + tid / ncs) * hc.C + rj_lo + tid % ncs) * hc.nbins;
-        }
-        __syncthreads();
+        ri_lo = band_of(u0 + 1, H, hc.R);
+        rj_lo = band_of(v0 + 1, W, hc.C);
+        ncs = band_of(min(v0 + kTileW, W - 2), W, hc.C) - rj_lo + 1;
+        nslots = (band_of(ue, H, hc.R) - ri_lo + 1) * ncs;
+        use_smem = nslots <= kWarpSlots;
     }
 
-    const int v = v0 + 4 * lane;
-    const int ub = u0 + warp * RPW;
-    const int ue = min(ub + RPW, H - 2);
-    if (v < W - 2 && ub < ue) {
+    if (v < W - 2) {
         const bool img_al = ((reinterpret_cast<uintptr_t>(jb.img) | (uintptr_t)jb.P) & 3u) == 0;
         const bool fast_ld = img_al && (v + 6 <= W);
         const bool cod_al = jb.codes != nullptr &&
                             ((reinterpret_cast<uintptr_t>(jb.codes) | (uintptr_t)jb.Pc) & 3u) == 0;
         const bool fast_st = cod_al && (v + 4 <= W - 2);
-        const int nvalid = min(4, W - 2 - v);
         bool valid[4];
+        int colb[4];  // per column: slot offset (smem) or region column (global)
 #pragma unroll
-        for (int t = 0; t < 4; ++t) valid[t] = t < nvalid;
-        int colb[4];
-        if constexpr (HIST) {
-#pragma unroll
-            for (int t = 0; t < 4; ++t) colb[t] = sm.col[4 * lane + t];
+        for (int t = 0; t < 4; ++t) {
+            valid[t] = v + t < W - 2;
+            colb[t] = 0;
+            if (HIST && valid[t]) {
+                const int rj = band_of(v + t + 1, W, hc.C);
+                colb[t] = use_smem ? (rj - rj_lo) * 256 : rj;
+            }
         }
+        // region row of image row x = u + 1, advanced as the rows go down
+        int ri = ri_lo, next_b = 0, rowb = 0;
+        if constexpr (HIST) {
+            next_b = band_lo(ri + 1, H, hc.R);
+            rowb = use_smem ? 0 : ri * hc.C;
+        }
+
         const size_t P = (size_t)jb.P;
-        const uint8_t* rp = jb.img + (size_t)ub * P;
+        const uint8_t* rp = jb.img + (size_t)u0 * P;
         const uint8_t* pf = rp + 3 * P;  // next input row to prefetch (one row ahead)
         Raw nx = load_raw(rp + 2 * P, v, W, fast_ld);
 
@@ -364,11 +347,15 @@ __device__ __forceinline__ void process_tile(const Job& jb, const HistCfg& hc, i
                 }
             }
             if constexpr (HIST) {
-                const int rowb = sm.row[u - u0];
+                while (u + 1 >= next_b) {  // crossed into the next region row
+                    ++ri;
+                    next_b = band_lo(ri + 1, H, hc.R);
+                    rowb = use_smem ? (ri - ri_lo) * ncs * 256 : ri * hc.C;
+                }
                 if (use_smem) {
 #pragma unroll
                     for (int t = 0; t < 4; ++t)
-                        if (valid[t]) atomicAdd(&sm.hist[rowb + colb[t] + (int)code[t]], 1u);
+                        if (valid[t]) atomicAdd(&wh[rowb + colb[t] + (int)code[t]], 1u);
                 } else {
 #pragma unroll
                     for (int t = 0; t < 4; ++t)
@@ -392,7 +379,7 @@ __device__ __forceinline__ void process_tile(const Job& jb, const HistCfg& hc, i
                 const uint32_t p23 = __byte_perm(code[2], code[3], 0x0040u);
                 emit(u, code, __byte_perm(p01, p23, 0x5410u));
             };
-            int u = ub;
+            int u = u0;
             for (; u + 3 <= ue; u += 3) {
                 step(r0, r1, r2, u);
                 step(r1, r2, r0, u + 1);
@@ -414,7 +401,7 @@ __device__ __forceinline__ void process_tile(const Job& jb, const HistCfg& hc, i
                 for (int t = 0; t < 4; ++t) code[t] = (packed >> (8 * t)) & 0xFFu;
                 emit(u, code, packed);
             };
-            int u = ub;
+            int u = u0;
             for (; u + 3 <= ue; u += 3) {
                 step(r0, r1, r2, u);
                 step(r1, r2, r0, u + 1);
@@ -426,13 +413,36 @@ __device__ __forceinline__ void process_tile(const Job& jb, const HistCfg& hc, i
     }
 
     if constexpr (HIST) {
-        __syncthreads();
         if (use_smem) {
-            const int nslots = geo.nslots;
-            for (int e = tid; e < nslots * 256; e += NT) {
-                const uint32_t c = sm.hist[e];
-                if (c) atomicAdd(&jb.hist[sm.slot_base[e >> 8] + bin_of(e & 255, hc, K)], c);
+            __syncwarp();
+            // Only codes that can occur are scanned: the C(8,k) codes with
+            // popcount k for LDP (bin = position in the list when compact,
+            // the code itself when raw), all 256 for LBP.
+            constexpr int NC = (MODE == kLDP) ? binom_ce(8, K) : 256;
+            constexpr int NI = (NC + 31) / 32;
+            int code_of[NI];
+#pragma unroll
+            for (int m = 0; m < NI; ++m) {
+                const int idx = lane + 32 * m;
+                code_of[m] = (MODE == kLDP) ? (idx < NC ? (int)__ldg(&g_code_list.code[K][idx]) : -1) : idx;
             }
+            for (int sl = 0; sl < nslots; ++sl) {
+                const int base = ((ri_lo + sl / ncs) * hc.C + rj_lo + sl % ncs) * hc.nbins;
+                uint32_t* hs = wh + sl * 256;
+#pragma unroll
+                for (int m = 0; m < NI; ++m) {
+                    const int code = code_of[m];
+                    if (code >= 0) {
+                        const uint32_t c = hs[code];
+                        if (c) {
+                            const int bin = (MODE == kLDP && hc.compact) ? lane + 32 * m : code;
+                            atomicAdd(&jb.hist[base + bin], c);
+                            hs[code] = 0;
+                        }
+                    }
+                }
+            }
+            __syncwarp();
         }
     }
 }

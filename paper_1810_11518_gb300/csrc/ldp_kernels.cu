@@ -1,4 +1,4 @@
-// Kernels of libldp for ONE tile variant (rows per warp x warps), compiled
+// Kernels of libldp for ONE tile variant (rows per warp tile x warps per CTA), compiled
 // once per variant with -DLDP_VAR_ID=<n> -DLDP_VAR_RPW=<rows> -DLDP_VAR_NW=<warps>
 // -DLDP_VAR_MB=<min CTAs per SM of the persistent kernel>:
 // the single-image fused kernel and the persistent batch kernel for every
@@ -19,7 +19,8 @@ namespace ldp {
 namespace LDP_VNS {
 
 struct VAR {
-    static constexpr int RPW = LDP_VAR_RPW, NW = LDP_VAR_NW, TH = LDP_VAR_RPW * LDP_VAR_NW, MB = LDP_VAR_MB;
+    // RPW: rows of a warp tile, NW: warps per CTA, MB: min CTAs per SM
+    static constexpr int RPW = LDP_VAR_RPW, NW = LDP_VAR_NW, MB = LDP_VAR_MB;
 };
 
 
@@ -44,81 +45,79 @@ __device__ __forceinline__ HistCfg to_hc(const HistArgs& h) {
     return c;
 }
 
-// ---------------- single image: one CTA per tile ----------------
+// Shared histograms: one private kWarpSlots x 256-bin histogram per warp.
+template <class V, bool HIST>
+struct WarpHists {
+    uint32_t h[HIST ? V::NW : 1][HIST ? kWarpSlots * 256 : 1];
+};
+
+template <class V, bool HIST>
+__device__ __forceinline__ uint32_t* warp_hist_zeroed(WarpHists<V, HIST>& s) {
+    if constexpr (!HIST) return nullptr;
+    uint32_t* wh = s.h[threadIdx.x >> 5];
+    for (int e = threadIdx.x & 31; e < kWarpSlots * 256; e += 32) wh[e] = 0;
+    __syncwarp();
+    return wh;
+}
+
+// ---------------- single image: one warp per tile ----------------
 template <int MODE, int K, class V, bool HIST>
 __global__ void __launch_bounds__(V::NW * 32, V::MB) k_plain(JobArgs ja, HistArgs ha) {
-    __shared__ Smem<V::TH> sm;
+    __shared__ WarpHists<V, HIST> sh;
     const Job jb = to_job(ja);
-    const HistCfg hc = to_hc(ha);
-    const int u0 = blockIdx.y * V::TH, v0 = blockIdx.x * kTileW;
-    TileGeo geo{0, 0, 1, 1, 1};
-    if (HIST) geo = tile_geo(jb.H, jb.W, hc, u0, v0, V::TH);  // uniform: every thread computes it
-    process_tile<MODE, K, V::RPW, V::NW, HIST>(jb, hc, u0, v0, geo, sm);
+    const int ntx = (jb.W - 2 + kTileW - 1) / kTileW;
+    const int nty = (jb.H - 2 + V::RPW - 1) / V::RPW;
+    const int w = blockIdx.x * V::NW + (threadIdx.x >> 5);
+    if (w >= ntx * nty) return;  // whole warp
+    uint32_t* wh = warp_hist_zeroed<V, HIST>(sh);
+    warp_tile<MODE, K, V::RPW, HIST>(jb, to_hc(ha), (w / ntx) * V::RPW, (w % ntx) * kTileW, wh);
 }
 
-// ---------------- persistent batch kernel ----------------
-// Asynchronous global -> shared copies.
-__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"((unsigned)__cvta_generic_to_shared(smem)),
-                 "l"(gmem)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"((unsigned)__cvta_generic_to_shared(smem)),
-                 "l"(gmem)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
-
-// Tiles come from an atomic counter (dynamic load balance across uneven
-// images).  Thread 0 takes the next tile, copies its descriptor into shared
-// memory asynchronously and publishes it at a barrier.
+// ---------------- persistent batch kernel: warps take tiles independently ----------------
+// Each warp takes tiles from an atomic counter: lane 0 takes the index and
+// the tile's image, lanes 0..10 load the image descriptor and its first tile
+// index together, and shuffles hand them to the whole warp.  No CTA-wide
+// barrier is ever needed.
 template <int MODE, int K, class V, bool HIST>
 __global__ void __launch_bounds__(V::NW * 32, V::MB) k_batch(BatchArgs a) {
-    __shared__ Smem<V::TH> sm;
+    __shared__ WarpHists<V, HIST> sh;
     const HistCfg hc = to_hc(a.hc);
+    const int lane = threadIdx.x & 31;
     const int total = *a.scr.total;
+    uint32_t* wh = warp_hist_zeroed<V, HIST>(sh);
     for (;;) {
-        if (threadIdx.x == 0) {
-            TileSlot& sl = sm.tile[0];
-            const int t = atomicAdd(a.scr.counter, 1);
-            if (t >= total) {
-                sl.u0 = -1;
-            } else {
-                const int img = a.scr.tile_img[t];
-                const uint64_t* src = reinterpret_cast<const uint64_t*>(a.descs + img);
-#pragma unroll
-                for (int w = 0; w < 5; ++w) cp_async8(&sm.stage[w], src + w);
-                cp_async4(&sm.stage[5], a.scr.prefix + img);
-                cp_async_wait_all();
-                const ldp_image_desc& d = *reinterpret_cast<const ldp_image_desc*>(&sm.stage[0]);
-                const int lt = t - (int)(sm.stage[5] & 0xFFFFFFFFu);
-                const int ntx = (d.W - 2 + kTileW - 1) / kTileW;
-                sl.u0 = (lt / ntx) * V::TH;
-                sl.v0 = (lt % ntx) * kTileW;
-                sl.job.img = d.img;
-                sl.job.H = d.H;
-                sl.job.W = d.W;
-                sl.job.P = d.pitch;
-                sl.job.codes = d.codes;
-                sl.job.Pc = d.code_pitch;
-                sl.job.hist = a.hist ? a.hist + d.hist_offset : nullptr;
-                if (HIST) sl.geo = tile_geo(d.H, d.W, hc, sl.u0, sl.v0, V::TH);
-            }
+        int t = 0, img = 0;
+        if (lane == 0) {
+            t = atomicAdd(a.scr.counter, 1);
+            if (t < total) img = a.scr.tile_img[t];
         }
-        __syncthreads();
-        const TileSlot& cur = sm.tile[0];
-        if (cur.u0 < 0) break;
-        const Job jb = cur.job;
-        const TileGeo geo = cur.geo;
-        process_tile<MODE, K, V::RPW, V::NW, HIST>(jb, hc, cur.u0, cur.v0, geo, sm);
-        __syncthreads();
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= total) break;
+        img = __shfl_sync(0xffffffffu, img, 0);
+        // descriptor words 0..9 (40 bytes) and the image's first tile index
+        uint32_t word = 0;
+        if (lane < 10) word = __ldg(reinterpret_cast<const unsigned int*>(a.descs + img) + lane);
+        else if (lane == 10) word = (uint32_t)__ldg(a.scr.prefix + img);
+        auto wd = [&](int i) { return __shfl_sync(0xffffffffu, word, i); };
+        Job jb;
+        jb.img = reinterpret_cast<const uint8_t*>((uint64_t)wd(0) | ((uint64_t)wd(1) << 32));
+        jb.H = (int)wd(2);
+        jb.W = (int)wd(3);
+        jb.P = (int)wd(4);
+        jb.Pc = (int)wd(5);
+        jb.codes = reinterpret_cast<uint8_t*>((uint64_t)wd(6) | ((uint64_t)wd(7) << 32));
+        const uint64_t hoff = (uint64_t)wd(8) | ((uint64_t)wd(9) << 32);
+        jb.hist = a.hist ? a.hist + hoff : nullptr;
+        const int lt = t - (int)wd(10);
+        const int ntx = (jb.W - 2 + kTileW - 1) / kTileW;
+        warp_tile<MODE, K, V::RPW, HIST>(jb, hc, (lt / ntx) * V::RPW, (lt % ntx) * kTileW, wh);
     }
 }
 
 // ---------------- dispatch ----------------
 cudaError_t launch_plain(int mode, int k, bool hist, const JobArgs& jb, const HistArgs& hc, cudaStream_t s) {
-    dim3 grid((jb.W - 2 + kTileW - 1) / kTileW, (jb.H - 2 + VAR::TH - 1) / VAR::TH);
+    const int tiles = ((jb.W - 2 + kTileW - 1) / kTileW) * ((jb.H - 2 + VAR::RPW - 1) / VAR::RPW);
+    dim3 grid((tiles + VAR::NW - 1) / VAR::NW);
     dim3 block(VAR::NW * 32);
 #define LDP_PLAIN(M, KK)                                                        \
     do {                                                                        \

@@ -40,11 +40,11 @@ struct BatchArgs {
     HistArgs hc;
 };
 
-// Tile variants X(id, rows per warp, warps, min CTAs per SM): tile = 128
-// columns x rows*warps; the last field caps registers per thread.
+// Tile variants X(id, rows per tile, warps per CTA, min CTAs per SM): each
+// warp owns a tile of 128 columns x rows; the last field caps registers.
 // ldp_kernels.cu is compiled once per entry (the build script reads this list).
 #define LDP_VARIANTS(X) \
-    X(0, 16, 4, 6) X(1, 16, 4, 7) X(2, 16, 4, 8) X(3, 32, 4, 6) X(4, 16, 8, 3) X(5, 8, 8, 3)
+    X(0, 64, 4, 6) X(1, 32, 4, 6) X(2, 64, 4, 5) X(3, 64, 4, 7) X(4, 128, 4, 6) X(5, 64, 8, 3) X(6, 32, 8, 3)
 
 #define LDP_DECLARE_VARIANT(ID, RPW, NW, MB)                                                              \
     namespace var##ID {                                                                                   \

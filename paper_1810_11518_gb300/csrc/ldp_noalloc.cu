@@ -29,7 +29,7 @@ namespace {
 
 constexpr int kNoAllocInts = 1 << 21;  // 8 MiB of work list
 constexpr int kMaxDevices = 64;
-constexpr int kTileRows = 64;   // variant 0: 16 rows per warp x 4 warps
+constexpr int kTileRows = 64;   // variant 0: warp tiles of 64 rows
 constexpr int kTileCols = 128;  // output columns per tile
 
 // [0] tile counter, [1] total tiles, [2] image count, [3..count+3] prefix,
