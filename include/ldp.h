@@ -165,6 +165,64 @@ LDP_API const char *ldp_variant_name(int variant);
 /* Variant used by the single-image entry points (default 0). */
 LDP_API int ldp_set_plain_variant(int variant);
 
+/* ---- serving: continuous batching of single-image requests ---- */
+
+/* A request runtime: images submitted one by one from host memory are
+ * admitted into a resident device arena when their buffers fit (admission by
+ * free device memory), gathered into batches as they arrive, and run by the
+ * batched kernel on `streams` concurrent streams, so batches overlap on the
+ * device (one copying in while another computes or copies out).  Results go
+ * back to the caller's host buffers; completions are collected with
+ * ldp_server_poll.  Each request gets exactly the codes and histograms that
+ * ldp_region_hist gives for the same image (LDP, k and rs of the config). */
+typedef struct ldp_server ldp_server;
+
+typedef struct {
+    int32_t max_batch;     /* requests per batch launch, >= 1 */
+    int32_t streams;       /* batches in flight, 1..16 */
+    uint64_t arena_bytes;  /* device memory for resident request buffers */
+    int32_t k;             /* LDP k, 1..7 */
+    ldp_region_spec rs;    /* region histograms of every request */
+    int32_t variant;       /* tile variant (-1: default) */
+    int32_t ctas_per_sm;   /* 0: as many as fit */
+} ldp_server_config;
+
+typedef struct {
+    uint64_t tag;          /* the caller's tag from ldp_server_submit */
+    uint64_t t_submit_ns;  /* steady-clock times: submitted, */
+    uint64_t t_start_ns;   /* admitted into a batch, */
+    uint64_t t_done_ns;    /* results in the caller's buffers */
+} ldp_completion;
+
+typedef struct {
+    uint64_t completed, pixels, batches, pending, arena_used, arena_bytes;
+} ldp_server_stats_t;
+
+/* Creates the runtime (allocates the arena and per-stream buffers, starts a
+ * dispatcher and a completion thread).  EINVAL on a bad config, ENOMEM when
+ * an allocation fails. */
+LDP_API int ldp_server_create(ldp_server **out, const ldp_server_config *cfg);
+
+/* Queues one request.  host_img (H x W, row pitch `pitch`) must stay valid
+ * and unchanged until the request completes (pinned memory lets the copy run
+ * asynchronously).  host_codes ((H-2) x (W-2), row pitch code_pitch) may be
+ * NULL; host_hist (R*C*nbins uint32) may be NULL.  Never blocks on the GPU.
+ * EINVAL for a bad shape or an image larger than the arena; ECUDA once the
+ * runtime has hit a CUDA error (the message says which). */
+LDP_API int ldp_server_submit(ldp_server *s, const uint8_t *host_img, int H, int W, int pitch,
+                              uint8_t *host_codes, int code_pitch, uint32_t *host_hist, uint64_t tag);
+
+/* Moves up to `max` completed requests (completion order) into out; *n_out
+ * is their number. */
+LDP_API int ldp_server_poll(ldp_server *s, ldp_completion *out, int max, int *n_out);
+
+/* Counters since creation. */
+LDP_API int ldp_server_stats(ldp_server *s, ldp_server_stats_t *out);
+
+/* Completes every submitted request, stops the threads and frees
+ * everything. */
+LDP_API int ldp_server_destroy(ldp_server *s);
+
 /* Batch run that allocates nothing, for callers that cannot call
  * cudaMalloc / cudaFree while they run (device memory budgeted once at
  * start-up, memory owned by another allocator's pool, or loops that must

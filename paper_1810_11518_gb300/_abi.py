@@ -26,6 +26,7 @@ EXPORTS = [
     "ldp_batch_plan_set_config", "ldp_num_variants", "ldp_variant_name", "ldp_set_plain_variant",
     "ldp_hist_bins", "ldp_bin_of_code", "ldp_last_error", "ldp_device_status", "ldp_version",
     "ldp_batch_plan_enable_timing", "ldp_batch_plan_kernel_times", "ldp_batch_run_noalloc",
+    "ldp_server_create", "ldp_server_submit", "ldp_server_poll", "ldp_server_stats", "ldp_server_destroy",
 ]
 
 
@@ -46,6 +47,22 @@ class ImageDesc(ctypes.Structure):
 
 
 assert ctypes.sizeof(ImageDesc) == 40
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("max_batch", ctypes.c_int32), ("streams", ctypes.c_int32), ("arena_bytes", ctypes.c_uint64),
+                ("k", ctypes.c_int32), ("rs", RegionSpec), ("variant", ctypes.c_int32),
+                ("ctas_per_sm", ctypes.c_int32)]
+
+
+class Completion(ctypes.Structure):
+    _fields_ = [("tag", ctypes.c_uint64), ("t_submit_ns", ctypes.c_uint64), ("t_start_ns", ctypes.c_uint64),
+                ("t_done_ns", ctypes.c_uint64)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in ("completed", "pixels", "batches", "pending", "arena_used",
+                                                "arena_bytes")]
 
 _lock = threading.Lock()
 _lib = None
@@ -84,6 +101,11 @@ def load(path: str | None = None):
             "ldp_batch_plan_enable_timing": [vp, i32],
             "ldp_batch_plan_kernel_times": [vp, ctypes.POINTER(ctypes.c_float), i32, ctypes.POINTER(i32)],
             "ldp_batch_run_noalloc": [vp, i32, u64, i32, i32, RegionSpec, vp, vp],
+            "ldp_server_create": [ctypes.POINTER(vp), ctypes.POINTER(ServerConfig)],
+            "ldp_server_submit": [vp, vp, i32, i32, i32, vp, i32, vp, u64],
+            "ldp_server_poll": [vp, ctypes.POINTER(Completion), i32, ctypes.POINTER(i32)],
+            "ldp_server_stats": [vp, ctypes.POINTER(ServerStats)],
+            "ldp_server_destroy": [vp],
         }
         for name, args in sig.items():
             fn = getattr(lib, name)

@@ -61,6 +61,7 @@ def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -
         (os.path.join(CSRC, "ldp_common.cu"), os.path.join(BUILD, "ldp_common.o"), []),
         (os.path.join(CSRC, "ldp_abi.cu"), os.path.join(BUILD, "ldp_abi.o"), []),
         (os.path.join(CSRC, "ldp_noalloc.cu"), os.path.join(BUILD, "ldp_noalloc.o"), []),
+        (os.path.join(CSRC, "ldp_server.cu"), os.path.join(BUILD, "ldp_server.o"), []),
     ]
     for vid, rpw, nw, mb in variants():
         units.append((os.path.join(CSRC, "ldp_kernels.cu"), os.path.join(BUILD, f"ldp_kernels_v{vid}.o"),
