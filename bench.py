@@ -26,6 +26,7 @@ max over ranks of the time.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import os
 import statistics
@@ -56,7 +57,8 @@ def parse():
     ap.add_argument("--variant", type=int, default=-1, help="tile variant (-1: autotune cache or 0)")
     ap.add_argument("--ctas-per-sm", type=int, default=0)
     ap.add_argument("--cpu-sample", type=int, default=1024, help="images in the oracle CPU sample")
-    ap.add_argument("--no-extras", action="store_true", help="skip plain / LBP / e2e / CPU legs")
+    ap.add_argument("--no-extras", action="store_true", help="skip plain / LBP / serving / CPU legs")
+    ap.add_argument("--serve-seconds", type=float, default=2.0, help="measured seconds per serving rate")
     return ap.parse_args()
 
 
@@ -207,7 +209,9 @@ def main():
     nb = ldp.hist_bins(k)
     hist_len = 7 * 6 * nb
     lay = ldp.BatchLayout.build([H] * n, [W] * n, hist_len=hist_len)
-    seeds = np.arange(n, dtype=np.uint64) + np.uint64(rank * n)
+    from paper_1810_11518_gb300 import multi
+
+    seeds = multi.rank_seeds(rank, n)
     # pinned host images, generated on the host cores
     h_img = torch.empty(lay.img_bytes, dtype=torch.uint8, pin_memory=True)
     synth.batch_into(h_img.numpy(), seeds, lay.Hs, lay.Ws, lay.pitches, lay.img_off, sigma=3.0)
@@ -243,11 +247,7 @@ def main():
         torch.cuda.synchronize(dev)
 
     def max_over_ranks(x: float) -> float:
-        if not pg:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        return float(t.item())
+        return multi.max_over_ranks(x, pg, dev)
 
     # ---- warm-up ----
     for _ in range(max(a.warmup, 3)):
@@ -278,18 +278,23 @@ def main():
 
     extras = {}
     if not a.no_extras:
-        # ---- plain per-image path on the same images ----
-        imgs = [d_img[int(lay.img_off[i]):int(lay.img_off[i]) + H * int(lay.pitches[i])].view(H, int(lay.pitches[i]))[:, :W]
-                for i in range(n)]
-        cviews = [d_codes[int(lay.code_off[i]):int(lay.code_off[i]) + (H - 2) * int(lay.code_pitches[i])]
-                  .view(H - 2, int(lay.code_pitches[i]))[:, :W - 2] for i in range(n)]
-        hviews = [d_hist[i * hist_len:(i + 1) * hist_len] for i in range(n)]
+        # ---- plain per-image path on the same images: one C-ABI call each ----
+        from paper_1810_11518_gb300 import _abi
+
+        lib = _abi.load()
+        rs = _abi.RegionSpec(7, 6, 1)
+        sptr = ctypes.c_void_p(stream.cuda_stream)
+        base_i, base_c, base_h = d_img.data_ptr(), d_codes.data_ptr(), d_hist.data_ptr()
+        calls = [(ctypes.c_void_p(base_i + int(lay.img_off[i])), H, W, int(lay.pitches[i]), k, rs,
+                  ctypes.c_void_p(base_h + 4 * i * hist_len), ctypes.c_void_p(base_c + int(lay.code_off[i])),
+                  int(lay.code_pitches[i]), sptr) for i in range(n)]
         ldp.set_plain_variant(0)
+        f = lib.ldp_region_hist
 
         def plain_step():
-            for i in range(n):
-                ldp.region_hist(imgs[i], k=k, regions=(7, 6), compact=True, hist=hviews[i], codes_out=cviews[i],
-                                stream=stream)
+            for c in calls:
+                if f(*c):
+                    _abi.check(1, "ldp_region_hist")
 
         plain_step()
         psteps = max(2, min(10, a.steps // 20))
@@ -302,7 +307,7 @@ def main():
         pms = max_over_ranks(e0.elapsed_time(e1)) / psteps
         extras["plain"] = {"value": round(world * pixels / (pms * 1e-3) / 1e6, 3), "unit": UNIT,
                            "ms_per_step": round(pms, 4), "launches_per_step": 2 * n,
-                           "note": "one ldp_region_hist call (memset + fused kernel) per image"}
+                           "note": "one ldp_region_hist C-ABI call (memset + fused kernel) per image"}
         extras["batched_over_plain"] = round(pms / ms_step, 3)
 
         # ---- LBP batched on the same images ----
@@ -352,6 +357,18 @@ def main():
 
     clk = clocks.stop()
 
+    if not a.no_extras and rank == 0 and a.serve_seconds > 0:
+        # ---- continuous-batching serving (Poisson arrivals, uneven 64..1024 sizes) ----
+        from paper_1810_11518_gb300 import serving
+
+        pool = serving.RequestPool(512, "uneven")
+        extras["serving"] = []
+        for rate in (5000, 20000, 50000):
+            with serving.Server(streams=3, max_batch=256, arena_bytes=1 << 30) as srv:
+                res = serving.run_load(srv, pool, rate, a.serve_seconds, warmup=0.5, seed=rate)
+            extras["serving"].append({kk: (round(vv, 4) if isinstance(vv, float) else vv) for kk, vv in res.items()})
+
+
     # ---- correctness spot check of the timed output (cheap): masses ----
     hsum = d_hist.view(n, hist_len).sum(dim=1)
     mass_ok = bool((hsum == (H - 2) * (W - 2)).all().item())
@@ -378,7 +395,8 @@ def main():
                          "frac": round(achieved_gbs / peak, 4), "traffic": None,
                          "kernel": "k_batch (persistent LDP codes + region hist)",
                          "kernel_ms": round(k_ms, 4), "algorithmic_bytes_per_launch": alg_bytes,
-                         "peak_source": f"{peak_src} hbm_gbs"},
+                         "peak_source": f"{peak_src} hbm_gbs",
+                         "binding_roof": "instruction issue (integer + FP32 per-pixel work); see profiles/"},
             "e2e": e2e,
             "gpu_launches": 3 * a.steps,
             "clocks": clk,

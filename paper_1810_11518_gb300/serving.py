@@ -112,6 +112,8 @@ def run_load(server: Server, pool: RequestPool, rate: float, seconds: float, war
     scheduled arrival to results in host memory (p50/p99, so client lag is
     included), the same from the actual submit, sustained Mpixel/s (their
     pixels over first arrival .. last completion), and the client's lag."""
+    import gc
+
     import torch
 
     rng = np.random.default_rng(seed)
@@ -129,6 +131,8 @@ def run_load(server: Server, pool: RequestPool, rate: float, seconds: float, war
     pick = rng.integers(0, pool.n, size=n_req)
     done: dict[int, tuple] = {}
     submitted_px = []
+    gc_was = gc.isenabled()
+    gc.disable()  # no collector pauses inside the arrival schedule
     t0_ns = time.monotonic_ns()  # the runtime stamps with the same monotonic clock
     lag_max = 0.0
     i = 0
@@ -159,6 +163,8 @@ def run_load(server: Server, pool: RequestPool, rate: float, seconds: float, war
         for c in server.poll():
             done[c[0]] = c
         time.sleep(0.0002)
+    if gc_was:
+        gc.enable()
     # measured window: requests arriving after warm-up
     lat, lat_sub, px, last_done, first_arr = [], [], 0, 0, None
     for tag in range(n_sub):
