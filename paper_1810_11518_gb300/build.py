@@ -29,15 +29,15 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found")
 
 
-def variants() -> list[tuple[int, int, int, int]]:
-    """(id, rows per warp, warps, min CTAs per SM) of every tile variant."""
+def variants() -> list[tuple[int, int, int, int, int]]:
+    """(id, rows per tile, warps per CTA, min CTAs per SM, staged) of every tile variant."""
     with open(os.path.join(CSRC, "ldp_launch.h")) as f:
         src = f.read()
     m = re.search(r"#define LDP_VARIANTS\(X\)((?:.*\\\n)*.*)", src)
     if not m:
         raise RuntimeError("LDP_VARIANTS not found")
     return [tuple(int(v) for v in t)
-            for t in re.findall(r"X\((\d+),\s*(\d+),\s*(\d+),\s*(\d+)\)", m.group(1))]
+            for t in re.findall(r"X\((\d+),\s*(\d+),\s*(\d+),\s*(\d+),\s*(\d+)\)", m.group(1))]
 
 
 def _sources_mtime() -> float:
@@ -63,9 +63,10 @@ def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -
         (os.path.join(CSRC, "ldp_noalloc.cu"), os.path.join(BUILD, "ldp_noalloc.o"), []),
         (os.path.join(CSRC, "ldp_server.cu"), os.path.join(BUILD, "ldp_server.o"), []),
     ]
-    for vid, rpw, nw, mb in variants():
+    for vid, rpw, nw, mb, st in variants():
         units.append((os.path.join(CSRC, "ldp_kernels.cu"), os.path.join(BUILD, f"ldp_kernels_v{vid}.o"),
-                      [f"-DLDP_VAR_ID={vid}", f"-DLDP_VAR_RPW={rpw}", f"-DLDP_VAR_NW={nw}", f"-DLDP_VAR_MB={mb}"]))
+                      [f"-DLDP_VAR_ID={vid}", f"-DLDP_VAR_RPW={rpw}", f"-DLDP_VAR_NW={nw}", f"-DLDP_VAR_MB={mb}",
+                       f"-DLDP_VAR_ST={st}"]))
     cmds = [[cc] + ARCH + FLAGS + inc + defs + ["-c", src, "-o", obj] for src, obj, defs in units]
     jobs = jobs or max(1, min(len(cmds), os.cpu_count() or 1))
     with cf.ThreadPoolExecutor(jobs) as ex:

@@ -56,7 +56,7 @@ int check_regions(int R, int C) {
 int run_plain(int mode, const uint8_t* img, int H, int W, int pitch, int k, int R, int C, int compact,
               uint32_t* hist, uint8_t* codes, int code_pitch, void* stream) {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    ldp::JobArgs jb{img, H, W, pitch, codes, code_pitch, hist};
+    ldp::JobArgs jb{img, H, W, pitch, codes, code_pitch, hist, ldp::status_word()};
     ldp::HistArgs hc{R, C, 256, 0};
     if (hist) {
         hc.nbins = (mode == 0 && compact) ? binom8(k) : 256;
@@ -246,6 +246,8 @@ static int batch_run(ldp_batch_plan* plan, int mode, const ldp_image_desc* d_des
     a.hc.C = plan->rs.C;
     a.hc.compact = (mode == 0 && plan->rs.compact) ? 1 : 0;
     a.hc.nbins = a.hc.compact ? binom8(plan->k) : 256;
+    a.status = ldp::status_word();
+    if (!a.status) return fail(LDP_ECUDA, "device status word not found");
     int occ = 0;
     cudaError_t e = ldp::batch_occupancy(mode, plan->k, d_hist != nullptr, plan->variant, &occ);
     if (e != cudaSuccess) return cuda_fail(e, "occupancy query");

@@ -6,15 +6,32 @@
 #include "ldp_device.cuh"
 #include "ldp_launch.h"
 
+#include <mutex>
+
 namespace ldp {
 
 // Device status word: bit 0 = a batch descriptor was rejected on the device,
-// bit 1 = a batch needed more tiles than its plan holds.
+// bit 1 = a batch needed more tiles than its plan holds, bit 2 = a bounded
+// wait for staged input gave up.
 __device__ int g_status;
 
-#define LDP_NAME(ID, RPW, NW, MB) "r" #RPW "w" #NW "b" #MB,
-#define LDP_TH(ID, RPW, NW, MB) (RPW),
-#define LDP_COUNT(ID, RPW, NW, MB) +1
+int* status_word() {
+    static std::mutex mu;
+    static int* addr[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!addr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_status) != cudaSuccess) return nullptr;
+        addr[dev] = static_cast<int*>(p);
+    }
+    return addr[dev];
+}
+
+#define LDP_NAME(ID, RPW, NW, MB, ST) "r" #RPW "w" #NW "b" #MB "t" #ST,
+#define LDP_TH(ID, RPW, NW, MB, ST) (RPW),
+#define LDP_COUNT(ID, RPW, NW, MB, ST) +1
 static const char* kVariantNames[] = {LDP_VARIANTS(LDP_NAME)};
 static const int kVariantTH[] = {LDP_VARIANTS(LDP_TH)};
 constexpr int kNumVariants = 0 LDP_VARIANTS(LDP_COUNT);
@@ -117,7 +134,7 @@ cudaError_t launch_batch_prep(int variant, const BatchArgs& a, cudaStream_t s) {
 cudaError_t launch_plain(int mode, int k, bool hist, int variant, const JobArgs& jb, const HistArgs& hc,
                          cudaStream_t s) {
     switch (variant) {
-#define LDP_CASE(ID, RPW, NW, MB) \
+#define LDP_CASE(ID, RPW, NW, MB, ST) \
     case ID: return var##ID::launch_plain(mode, k, hist, jb, hc, s);
         LDP_VARIANTS(LDP_CASE)
 #undef LDP_CASE
@@ -128,7 +145,7 @@ cudaError_t launch_plain(int mode, int k, bool hist, int variant, const JobArgs&
 cudaError_t launch_batch_main(int mode, int k, bool hist, int variant, int grid, const BatchArgs& a,
                               cudaStream_t s) {
     switch (variant) {
-#define LDP_CASE(ID, RPW, NW, MB) \
+#define LDP_CASE(ID, RPW, NW, MB, ST) \
     case ID: return var##ID::launch_batch_main(mode, k, hist, grid, a, s);
         LDP_VARIANTS(LDP_CASE)
 #undef LDP_CASE
@@ -138,7 +155,7 @@ cudaError_t launch_batch_main(int mode, int k, bool hist, int variant, int grid,
 
 cudaError_t batch_occupancy(int mode, int k, bool hist, int variant, int* blocks_per_sm) {
     switch (variant) {
-#define LDP_CASE(ID, RPW, NW, MB) \
+#define LDP_CASE(ID, RPW, NW, MB, ST) \
     case ID: return var##ID::batch_occupancy(mode, k, hist, blocks_per_sm);
         LDP_VARIANTS(LDP_CASE)
 #undef LDP_CASE

@@ -19,6 +19,7 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 
 namespace ldp {
 
@@ -274,7 +275,61 @@ __device__ __forceinline__ int bin_of(int code, const HistCfg& hc, int k) {
     return hc.compact ? (int)__ldg(&g_bin_table.bin[k][code]) : code;
 }
 
-constexpr int kWarpSlots = 8;  // region slots a warp tile may touch and still count in smem
+constexpr int kWarpSlots = 6;  // region slots a warp tile may touch and still count in smem
+
+// Staged input (bulk-copy engine): per warp a ring of kStages stages of
+// kStageRows image rows, kRowBytes bytes each (the 130 bytes a 128-column
+// tile reads, rounded up to 16), filled by cp.async.bulk and completed on one
+// mbarrier per stage.
+constexpr int kStageRows = 8, kStages = 3, kRowBytes = 144;
+constexpr int kSpinLimit = 1 << 22;  // bounded mbarrier waits
+constexpr int kStatusWaitTimeout = 4;  // device status bit: a bounded wait gave up
+
+struct WarpRing {
+    alignas(128) uint8_t row[kStages][kStageRows][kRowBytes];
+    alignas(8) unsigned long long bar[kStages];
+};
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, unsigned long long* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Lane 0 of each warp initialises the warp's ring barriers (once per kernel).
+__device__ __forceinline__ void ring_init(WarpRing* ring) {
+    if ((threadIdx.x & 31) == 0) {
+        for (int s = 0; s < kStages; ++s) mbar_init(&ring->bar[s], 1);
+        mbar_fence_init();
+    }
+    __syncwarp();
+}
 
 // Lower bound of band b: floor(b*n/nb).
 __device__ __forceinline__ int band_lo(int b, int n, int nb) {
@@ -283,12 +338,16 @@ __device__ __forceinline__ int band_lo(int b, int n, int nb) {
 
 // One warp processes one tile of RW output rows x 128 output columns at
 // (u0, v0): lane l owns columns v0+4l .. v0+4l+3 and walks down the rows.
-// With HIST the codes are counted in the warp's private shared histogram
-// `wh` (kWarpSlots x 256 raw bins, all zero on entry and on exit): the flush
-// adds every non-zero bin to the global histogram and resets it.  Region
-// grids too fine for kWarpSlots slots count straight into global memory.
-template <int MODE, int K, int RW, bool HIST>
-__device__ __forceinline__ void warp_tile(const Job& jb, const HistCfg& hc, int u0, int v0, uint32_t* wh) {
+// Input rows come either from per-lane global loads one row ahead, or
+// (STAGED, for 16-byte aligned images) from the warp's bulk-copy ring, two
+// stages ahead.  With HIST the codes are counted in the warp's private shared
+// histogram `wh` (kWarpSlots x 256 raw bins, all zero on entry and on exit):
+// the flush adds every non-zero bin to the global histogram and resets it.
+// Region grids too fine for kWarpSlots slots count straight into global
+// memory.  `ph` holds the ring's per-stage wait parities across tiles.
+template <int MODE, int K, int RW, bool HIST, bool STAGED>
+__device__ __forceinline__ void warp_tile(const Job& jb, const HistCfg& hc, int u0, int v0, uint32_t* wh,
+                                          WarpRing* ring, uint32_t& ph, int* status) {
     const int lane = threadIdx.x & 31;
     const int H = jb.H, W = jb.W;
     const int ue = min(u0 + RW, H - 2);  // output rows [u0, ue) = image rows [u0+1, ue]
@@ -305,111 +364,201 @@ __device__ __forceinline__ void warp_tile(const Job& jb, const HistCfg& hc, int 
         use_smem = nslots <= kWarpSlots;
     }
 
-    if (v < W - 2) {
-        const bool img_al = ((reinterpret_cast<uintptr_t>(jb.img) | (uintptr_t)jb.P) & 3u) == 0;
-        const bool fast_ld = img_al && (v + 6 <= W);
-        const bool cod_al = jb.codes != nullptr &&
-                            ((reinterpret_cast<uintptr_t>(jb.codes) | (uintptr_t)jb.Pc) & 3u) == 0;
-        const bool fast_st = cod_al && (v + 4 <= W - 2);
-        bool valid[4];
-        int colb[4];  // per column: slot offset (smem) or region column (global)
+    const size_t P = (size_t)jb.P;
+    // the ring holds bytes v0 .. v0+nbytes of every input row; the bulk-copy
+    // engine fills rows when the image is 16-byte aligned, except the last
+    // image row when it would read past W (no pitch padding is guaranteed
+    // there); such rows are copied by the warp with plain loads
+    const int nbytes = min(kRowBytes, (W - v0 + 15) & ~15);
+    const bool bulk_img = ((reinterpret_cast<uintptr_t>(jb.img) | P) & 15u) == 0;
+    constexpr bool staged = STAGED;
+
+    const bool img_al = ((reinterpret_cast<uintptr_t>(jb.img) | P) & 3u) == 0;
+    const bool fast_ld = img_al && (v + 6 <= W);
+    const bool cod_al =
+        jb.codes != nullptr && ((reinterpret_cast<uintptr_t>(jb.codes) | (uintptr_t)jb.Pc) & 3u) == 0;
+    const bool fast_st = cod_al && (v + 4 <= W - 2);
+    bool valid[4];
+    int colb[4];  // per column: slot offset (smem) or region column (global)
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
-            valid[t] = v + t < W - 2;
-            colb[t] = 0;
-            if (HIST && valid[t]) {
-                const int rj = band_of(v + t + 1, W, hc.C);
-                colb[t] = use_smem ? (rj - rj_lo) * 256 : rj;
+    for (int t = 0; t < 4; ++t) {
+        valid[t] = v + t < W - 2;
+        colb[t] = 0;
+        if (HIST && valid[t]) {
+            const int rj = band_of(v + t + 1, W, hc.C);
+            colb[t] = use_smem ? (rj - rj_lo) * 256 : rj;
+        }
+    }
+    // region row of image row x = u + 1, advanced as the rows go down
+    int ri = ri_lo, next_b = 0, rowb = 0;
+    if constexpr (HIST) {
+        next_b = band_lo(ri + 1, H, hc.R);
+        rowb = use_smem ? 0 : ri * hc.C;
+    }
+
+    // codes of output row u -> code map and histogram
+    auto emit = [&](int u, const uint32_t (&code)[4], uint32_t packed) {
+        if (jb.codes) {
+            uint8_t* cp = jb.codes + (size_t)u * (size_t)jb.Pc + v;
+            if (fast_st) {
+                *reinterpret_cast<uint32_t*>(cp) = packed;
+            } else {
+#pragma unroll
+                for (int t = 0; t < 4; ++t)
+                    if (valid[t]) cp[t] = (uint8_t)code[t];
             }
         }
-        // region row of image row x = u + 1, advanced as the rows go down
-        int ri = ri_lo, next_b = 0, rowb = 0;
         if constexpr (HIST) {
-            next_b = band_lo(ri + 1, H, hc.R);
-            rowb = use_smem ? 0 : ri * hc.C;
+            while (u + 1 >= next_b) {  // crossed into the next region row
+                ++ri;
+                next_b = band_lo(ri + 1, H, hc.R);
+                rowb = use_smem ? (ri - ri_lo) * ncs * 256 : ri * hc.C;
+            }
+            if (use_smem) {
+#pragma unroll
+                for (int t = 0; t < 4; ++t)
+                    if (valid[t]) atomicAdd(&wh[rowb + colb[t] + (int)code[t]], 1u);
+            } else {
+#pragma unroll
+                for (int t = 0; t < 4; ++t)
+                    if (valid[t])
+                        atomicAdd(&jb.hist[(size_t)(rowb + colb[t]) * hc.nbins + bin_of((int)code[t], hc, K)], 1u);
+            }
         }
+    };
+    auto codes_of_row = [&](const auto& A, const auto& B, const auto& C, uint32_t (&code)[4]) -> uint32_t {
+        if constexpr (MODE == kLDP) {
+            ldp_row4<K>(A, B, C, code);
+            const uint32_t p01 = __byte_perm(code[0], code[1], 0x0040u);
+            const uint32_t p23 = __byte_perm(code[2], code[3], 0x0040u);
+            return __byte_perm(p01, p23, 0x5410u);
+        } else {
+            const uint32_t packed = lbp_row4(A, B, C);
+#pragma unroll
+            for (int t = 0; t < 4; ++t) code[t] = (packed >> (8 * t)) & 0xFFu;
+            return packed;
+        }
+    };
+    using Row = std::conditional_t<MODE == kLDP, FRow, BRow>;
+    auto unpack = [&](const Raw& w, Row& r) {
+        if constexpr (MODE == kLDP)
+            unpack_frow(w, r);
+        else
+            unpack_brow(w, r);
+    };
 
-        const size_t P = (size_t)jb.P;
+    if constexpr (staged) {
+        // all lanes run the ring protocol; lanes past the interior compute
+        // nothing that is stored or counted (valid[] is false)
+        const int nrows = ue - u0 + 2;  // input rows u0 .. ue+1
+        const uint8_t* base = jb.img + (size_t)u0 * P + v0;
+        uint32_t pend = 0;  // stages filled and not yet waited
+        bool ok = true;
+        auto fill = [&](int g) {
+            const int r0 = g * kStageRows, n = min(kStageRows, nrows - r0);
+            if (n <= 0) return;
+            const int sidx = g % kStages;
+            // rows [r0, r0 + nb) go through the bulk-copy engine
+            int nb = bulk_img ? n : 0;
+            if (nb > 0 && u0 + r0 + nb - 1 == H - 1 && v0 + nbytes > W) --nb;
+            __syncwarp();
+            if (lane == 0) {
+                fence_proxy_async();
+                mbar_expect_tx(&ring->bar[sidx], (uint32_t)(nb * nbytes));  // 0 bytes: the phase completes now
+            }
+            __syncwarp();
+            if (lane < nb) {
+                fence_proxy_async();
+                bulk_g2s(ring->row[sidx][lane], base + (size_t)(r0 + lane) * P, (uint32_t)nbytes, &ring->bar[sidx]);
+            }
+            for (int r = nb; r < n; ++r) {  // plain copies, zero past column W-1
+                const uint8_t* src = base + (size_t)(r0 + r) * P;
+                uint8_t* dst = ring->row[sidx][r];
+                for (int b = lane; b < kRowBytes; b += 32) dst[b] = (v0 + b < W) ? __ldg(src + b) : (uint8_t)0;
+            }
+            __syncwarp();
+            pend |= 1u << sidx;
+        };
+        auto wait = [&](int g) {
+            const int sidx = g % kStages;
+            const uint32_t par = (ph >> sidx) & 1u;
+            bool done = false;
+            for (int i = 0; i < kSpinLimit && !done; ++i) done = mbar_try_wait(&ring->bar[sidx], par);
+            if (done) {
+                ph ^= 1u << sidx;
+                pend &= ~(1u << sidx);
+            } else {
+                ok = false;
+            }
+        };
+        auto read = [&](int ir) {
+            const uint8_t* q = ring->row[(ir / kStageRows) % kStages][ir % kStageRows] + 4 * lane;
+            Raw r;
+            r.w0 = *reinterpret_cast<const uint32_t*>(q);
+            r.w1 = *reinterpret_cast<const uint16_t*>(q + 4);
+            return r;
+        };
+        for (int g = 0; g < kStages; ++g) fill(g);
+        wait(0);
+        Row r0, r1, r2;
+        if (ok) {
+            unpack(read(0), r0);
+            unpack(read(1), r1);
+        }
+        auto step = [&](const Row& A, const Row& B, Row& C, int ou) {
+            const int ir = ou + 2;  // input row that becomes C
+            if (ir % kStageRows == 0) wait(ir / kStageRows);
+            if (!ok) return;
+            unpack(read(ir), C);
+            if (ir % kStageRows == kStageRows - 1) fill(ir / kStageRows + kStages);  // stage fully read
+            uint32_t code[4];
+            const uint32_t packed = codes_of_row(A, B, C, code);
+            emit(u0 + ou, code, packed);
+        };
+        const int nout = ue - u0;
+        int ou = 0;
+        for (; ou + 3 <= nout && ok; ou += 3) {
+            step(r0, r1, r2, ou);
+            step(r1, r2, r0, ou + 1);
+            step(r2, r0, r1, ou + 2);
+        }
+        if (ok && ou < nout) step(r0, r1, r2, ou);
+        if (ok && ou + 1 < nout) step(r1, r2, r0, ou + 1);
+        // every filled stage is consumed on the way; after a timeout, give the
+        // copies still in flight a bounded chance to land before returning
+        if (!ok || pend) {
+            if (lane == 0) atomicOr(status, kStatusWaitTimeout);
+            for (int sidx = 0; sidx < kStages; ++sidx)
+                if (pend >> sidx & 1u) {
+                    const uint32_t par = (ph >> sidx) & 1u;
+                    bool done = false;
+                    for (int i = 0; i < kSpinLimit && !done; ++i) done = mbar_try_wait(&ring->bar[sidx], par);
+                    if (done) ph ^= 1u << sidx;
+                }
+        }
+    } else if (v < W - 2) {  // per-lane global loads, one row ahead
         const uint8_t* rp = jb.img + (size_t)u0 * P;
         const uint8_t* pf = rp + 3 * P;  // next input row to prefetch (one row ahead)
         Raw nx = load_raw(rp + 2 * P, v, W, fast_ld);
-
-        // codes of output row u -> code map and histogram
-        auto emit = [&](int u, const uint32_t (&code)[4], uint32_t packed) {
-            if (jb.codes) {
-                uint8_t* cp = jb.codes + (size_t)u * (size_t)jb.Pc + v;
-                if (fast_st) {
-                    *reinterpret_cast<uint32_t*>(cp) = packed;
-                } else {
-#pragma unroll
-                    for (int t = 0; t < 4; ++t)
-                        if (valid[t]) cp[t] = (uint8_t)code[t];
-                }
-            }
-            if constexpr (HIST) {
-                while (u + 1 >= next_b) {  // crossed into the next region row
-                    ++ri;
-                    next_b = band_lo(ri + 1, H, hc.R);
-                    rowb = use_smem ? (ri - ri_lo) * ncs * 256 : ri * hc.C;
-                }
-                if (use_smem) {
-#pragma unroll
-                    for (int t = 0; t < 4; ++t)
-                        if (valid[t]) atomicAdd(&wh[rowb + colb[t] + (int)code[t]], 1u);
-                } else {
-#pragma unroll
-                    for (int t = 0; t < 4; ++t)
-                        if (valid[t])
-                            atomicAdd(&jb.hist[(size_t)(rowb + colb[t]) * hc.nbins + bin_of((int)code[t], hc, K)], 1u);
-                }
-            }
+        Row r0, r1, r2;
+        unpack(load_raw(rp, v, W, fast_ld), r0);
+        unpack(load_raw(rp + P, v, W, fast_ld), r1);
+        auto step = [&](const Row& A, const Row& B, Row& C, int u) {
+            unpack(nx, C);
+            if (u + 1 < ue) nx = load_raw(pf, v, W, fast_ld);
+            pf += P;
+            uint32_t code[4];
+            const uint32_t packed = codes_of_row(A, B, C, code);
+            emit(u, code, packed);
         };
-
-        if constexpr (MODE == kLDP) {
-            FRow r0, r1, r2;
-            unpack_frow(load_raw(rp, v, W, fast_ld), r0);
-            unpack_frow(load_raw(rp + P, v, W, fast_ld), r1);
-            auto step = [&](const FRow& A, const FRow& B, FRow& C, int u) {
-                unpack_frow(nx, C);
-                if (u + 1 < ue) nx = load_raw(pf, v, W, fast_ld);
-                pf += P;
-                uint32_t code[4];
-                ldp_row4<K>(A, B, C, code);
-                const uint32_t p01 = __byte_perm(code[0], code[1], 0x0040u);
-                const uint32_t p23 = __byte_perm(code[2], code[3], 0x0040u);
-                emit(u, code, __byte_perm(p01, p23, 0x5410u));
-            };
-            int u = u0;
-            for (; u + 3 <= ue; u += 3) {
-                step(r0, r1, r2, u);
-                step(r1, r2, r0, u + 1);
-                step(r2, r0, r1, u + 2);
-            }
-            if (u < ue) step(r0, r1, r2, u);
-            if (u + 1 < ue) step(r1, r2, r0, u + 1);
-        } else {
-            BRow r0, r1, r2;
-            unpack_brow(load_raw(rp, v, W, fast_ld), r0);
-            unpack_brow(load_raw(rp + P, v, W, fast_ld), r1);
-            auto step = [&](const BRow& A, const BRow& B, BRow& C, int u) {
-                unpack_brow(nx, C);
-                if (u + 1 < ue) nx = load_raw(pf, v, W, fast_ld);
-                pf += P;
-                const uint32_t packed = lbp_row4(A, B, C);
-                uint32_t code[4];
-#pragma unroll
-                for (int t = 0; t < 4; ++t) code[t] = (packed >> (8 * t)) & 0xFFu;
-                emit(u, code, packed);
-            };
-            int u = u0;
-            for (; u + 3 <= ue; u += 3) {
-                step(r0, r1, r2, u);
-                step(r1, r2, r0, u + 1);
-                step(r2, r0, r1, u + 2);
-            }
-            if (u < ue) step(r0, r1, r2, u);
-            if (u + 1 < ue) step(r1, r2, r0, u + 1);
+        int u = u0;
+        for (; u + 3 <= ue; u += 3) {
+            step(r0, r1, r2, u);
+            step(r1, r2, r0, u + 1);
+            step(r2, r0, r1, u + 2);
         }
+        if (u < ue) step(r0, r1, r2, u);
+        if (u + 1 < ue) step(r1, r2, r0, u + 1);
     }
 
     if constexpr (HIST) {
@@ -427,7 +576,7 @@ __device__ __forceinline__ void warp_tile(const Job& jb, const HistCfg& hc, int 
                 code_of[m] = (MODE == kLDP) ? (idx < NC ? (int)__ldg(&g_code_list.code[K][idx]) : -1) : idx;
             }
             for (int sl = 0; sl < nslots; ++sl) {
-                const int base = ((ri_lo + sl / ncs) * hc.C + rj_lo + sl % ncs) * hc.nbins;
+                const int hbase = ((ri_lo + sl / ncs) * hc.C + rj_lo + sl % ncs) * hc.nbins;
                 uint32_t* hs = wh + sl * 256;
 #pragma unroll
                 for (int m = 0; m < NI; ++m) {
@@ -436,7 +585,7 @@ __device__ __forceinline__ void warp_tile(const Job& jb, const HistCfg& hc, int 
                         const uint32_t c = hs[code];
                         if (c) {
                             const int bin = (MODE == kLDP && hc.compact) ? lane + 32 * m : code;
-                            atomicAdd(&jb.hist[base + bin], c);
+                            atomicAdd(&jb.hist[hbase + bin], c);
                             hs[code] = 0;
                         }
                     }

@@ -1,6 +1,6 @@
 // Kernels of libldp for ONE tile variant (rows per warp tile x warps per CTA), compiled
 // once per variant with -DLDP_VAR_ID=<n> -DLDP_VAR_RPW=<rows> -DLDP_VAR_NW=<warps>
-// -DLDP_VAR_MB=<min CTAs per SM of the persistent kernel>:
+// -DLDP_VAR_MB=<min CTAs per SM> -DLDP_VAR_ST=<1: rows staged through the bulk-copy engine>:
 // the single-image fused kernel and the persistent batch kernel for every
 // (mode, k, histogram) combination, plus their launchers.
 #include <cuda_runtime.h>
@@ -9,7 +9,7 @@
 #include "ldp_launch.h"
 
 #ifndef LDP_VAR_ID
-#error "compile with -DLDP_VAR_ID, -DLDP_VAR_RPW, -DLDP_VAR_NW and -DLDP_VAR_MB"
+#error "compile with -DLDP_VAR_ID, -DLDP_VAR_RPW, -DLDP_VAR_NW, -DLDP_VAR_MB and -DLDP_VAR_ST"
 #endif
 #define LDP_CAT2(a, b) a##b
 #define LDP_CAT(a, b) LDP_CAT2(a, b)
@@ -19,8 +19,10 @@ namespace ldp {
 namespace LDP_VNS {
 
 struct VAR {
-    // RPW: rows of a warp tile, NW: warps per CTA, MB: min CTAs per SM
+    // RPW: rows of a warp tile, NW: warps per CTA, MB: min CTAs per SM,
+    // ST: input rows staged through the bulk-copy ring
     static constexpr int RPW = LDP_VAR_RPW, NW = LDP_VAR_NW, MB = LDP_VAR_MB;
+    static constexpr bool ST = LDP_VAR_ST != 0;
 };
 
 
@@ -45,16 +47,24 @@ __device__ __forceinline__ HistCfg to_hc(const HistArgs& h) {
     return c;
 }
 
-// Shared histograms: one private kWarpSlots x 256-bin histogram per warp.
+// Shared memory of a CTA: per warp a private kWarpSlots x 256-bin histogram
+// (with HIST) and a bulk-copy ring (staged variants).
 template <class V, bool HIST>
-struct WarpHists {
+struct WarpSmem {
     uint32_t h[HIST ? V::NW : 1][HIST ? kWarpSlots * 256 : 1];
+    WarpRing ring[V::ST ? V::NW : 1];
 };
 
 template <class V, bool HIST>
-__device__ __forceinline__ uint32_t* warp_hist_zeroed(WarpHists<V, HIST>& s) {
+__device__ __forceinline__ uint32_t* warp_setup(WarpSmem<V, HIST>& s, WarpRing** ring) {
+    const int w = threadIdx.x >> 5;
+    *ring = nullptr;
+    if constexpr (V::ST) {
+        *ring = &s.ring[w];
+        ring_init(*ring);
+    }
     if constexpr (!HIST) return nullptr;
-    uint32_t* wh = s.h[threadIdx.x >> 5];
+    uint32_t* wh = s.h[w];
     for (int e = threadIdx.x & 31; e < kWarpSlots * 256; e += 32) wh[e] = 0;
     __syncwarp();
     return wh;
@@ -63,14 +73,17 @@ __device__ __forceinline__ uint32_t* warp_hist_zeroed(WarpHists<V, HIST>& s) {
 // ---------------- single image: one warp per tile ----------------
 template <int MODE, int K, class V, bool HIST>
 __global__ void __launch_bounds__(V::NW * 32, V::MB) k_plain(JobArgs ja, HistArgs ha) {
-    __shared__ WarpHists<V, HIST> sh;
+    __shared__ WarpSmem<V, HIST> sh;
     const Job jb = to_job(ja);
     const int ntx = (jb.W - 2 + kTileW - 1) / kTileW;
     const int nty = (jb.H - 2 + V::RPW - 1) / V::RPW;
     const int w = blockIdx.x * V::NW + (threadIdx.x >> 5);
     if (w >= ntx * nty) return;  // whole warp
-    uint32_t* wh = warp_hist_zeroed<V, HIST>(sh);
-    warp_tile<MODE, K, V::RPW, HIST>(jb, to_hc(ha), (w / ntx) * V::RPW, (w % ntx) * kTileW, wh);
+    WarpRing* ring;
+    uint32_t* wh = warp_setup<V, HIST>(sh, &ring);
+    uint32_t ph = 0;
+    warp_tile<MODE, K, V::RPW, HIST, V::ST>(jb, to_hc(ha), (w / ntx) * V::RPW, (w % ntx) * kTileW, wh, ring, ph,
+                                            ja.status);
 }
 
 // ---------------- persistent batch kernel: warps take tiles independently ----------------
@@ -80,11 +93,13 @@ __global__ void __launch_bounds__(V::NW * 32, V::MB) k_plain(JobArgs ja, HistArg
 // barrier is ever needed.
 template <int MODE, int K, class V, bool HIST>
 __global__ void __launch_bounds__(V::NW * 32, V::MB) k_batch(BatchArgs a) {
-    __shared__ WarpHists<V, HIST> sh;
+    __shared__ WarpSmem<V, HIST> sh;
     const HistCfg hc = to_hc(a.hc);
     const int lane = threadIdx.x & 31;
     const int total = *a.scr.total;
-    uint32_t* wh = warp_hist_zeroed<V, HIST>(sh);
+    WarpRing* ring;
+    uint32_t* wh = warp_setup<V, HIST>(sh, &ring);
+    uint32_t ph = 0;
     for (;;) {
         int t = 0, img = 0;
         if (lane == 0) {
@@ -110,7 +125,8 @@ __global__ void __launch_bounds__(V::NW * 32, V::MB) k_batch(BatchArgs a) {
         jb.hist = a.hist ? a.hist + hoff : nullptr;
         const int lt = t - (int)wd(10);
         const int ntx = (jb.W - 2 + kTileW - 1) / kTileW;
-        warp_tile<MODE, K, V::RPW, HIST>(jb, hc, (lt / ntx) * V::RPW, (lt % ntx) * kTileW, wh);
+        warp_tile<MODE, K, V::RPW, HIST, V::ST>(jb, hc, (lt / ntx) * V::RPW, (lt % ntx) * kTileW, wh, ring, ph,
+                                                a.status);
     }
 }
 

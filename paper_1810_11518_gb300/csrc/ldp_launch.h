@@ -16,6 +16,7 @@ struct JobArgs {
     uint8_t* codes;
     int Pc;
     uint32_t* hist;
+    int* status;  // device status word
 };
 
 struct HistArgs {
@@ -38,15 +39,17 @@ struct BatchArgs {
     int max_tiles;
     BatchScratch scr;
     HistArgs hc;
+    int* status;  // device status word
 };
 
-// Tile variants X(id, rows per tile, warps per CTA, min CTAs per SM): each
-// warp owns a tile of 128 columns x rows; the last field caps registers.
+// Tile variants X(id, rows per tile, warps per CTA, min CTAs per SM, staged):
+// each warp owns a tile of 128 columns x rows; MB caps registers; staged = 1
+// feeds the rows through the bulk-copy (TMA) engine into a shared ring.
 // ldp_kernels.cu is compiled once per entry (the build script reads this list).
-#define LDP_VARIANTS(X) \
-    X(0, 64, 4, 6) X(1, 32, 4, 6) X(2, 64, 4, 5) X(3, 64, 4, 7) X(4, 128, 4, 6) X(5, 64, 8, 3) X(6, 32, 8, 3)
+#define LDP_VARIANTS(X)                                                                          \
+    X(0, 64, 4, 5, 0) X(1, 64, 4, 6, 0) X(2, 64, 8, 3, 0) X(3, 64, 4, 4, 1) X(4, 128, 4, 4, 1)
 
-#define LDP_DECLARE_VARIANT(ID, RPW, NW, MB)                                                              \
+#define LDP_DECLARE_VARIANT(ID, RPW, NW, MB, ST)                                                              \
     namespace var##ID {                                                                                   \
     cudaError_t launch_plain(int mode, int k, bool hist, const JobArgs& jb, const HistArgs& hc,           \
                              cudaStream_t s);                                                             \
@@ -72,5 +75,7 @@ cudaError_t launch_batch_main(int mode, int k, bool hist, int variant, int grid,
 cudaError_t batch_occupancy(int mode, int k, bool hist, int variant, int* blocks_per_sm);
 
 cudaError_t read_clear_status(cudaStream_t s, int* out);
+// Device address of the status word on the current device (looked up once per device).
+int* status_word();
 
 }  // namespace ldp

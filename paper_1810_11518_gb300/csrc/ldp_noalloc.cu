@@ -102,6 +102,7 @@ extern "C" LDP_API int ldp_batch_run_noalloc(const ldp_image_desc* d_descs, int 
     a.scr.total = base + 1;
     a.scr.prefix = base + 3;
     a.scr.tile_img = base + 3 + (count + 1);
+    a.status = ldp::status_word();
     a.hc.R = rs.R;
     a.hc.C = rs.C;
     a.hc.compact = rs.compact;

@@ -111,26 +111,45 @@ def test_edge_sizes(env, H, W):
 
 
 def test_pitch_and_unaligned_pointers(env):
+    """Any pitch and any alignment, for every tile variant (staged variants
+    copy rows they cannot bulk-copy with plain loads)."""
     torch, ldp, oracle, synth = env
     img = synth.image(11, 77, 150, 3.0)
     h_ref, c_ref = oracle.extract(img, k=3, R=3, C=4, compact=True)
-    for pitch, off in ((150, 0), (160, 0), (151, 0), (163, 5), (150, 1), (256, 3)):
-        big = torch.zeros(77 * pitch + off + 64, dtype=torch.uint8, device="cuda")
-        view = big[off:off + 77 * pitch].view(77, pitch)[:, :150]
-        view.copy_(_dev(torch, img))
-        for cpitch, coff in ((148, 0), (149, 1), (160, 7)):
-            cbuf = torch.zeros((75 * cpitch + coff,), dtype=torch.uint8, device="cuda")
-            cview = cbuf[coff:coff + 75 * cpitch].view(75, cpitch)[:, :148]
-            h, c = ldp.region_hist(view, k=3, regions=(3, 4), codes_out=cview)
+    try:
+        for v in range(ldp.num_variants()):
+            ldp.set_plain_variant(v)
+            for pitch, off in ((150, 0), (160, 0), (151, 0), (163, 5), (150, 1), (256, 3)):
+                big = torch.zeros(77 * pitch + off + 64, dtype=torch.uint8, device="cuda")
+                view = big[off:off + 77 * pitch].view(77, pitch)[:, :150]
+                view.copy_(_dev(torch, img))
+                for cpitch, coff in ((148, 0), (149, 1), (160, 7)):
+                    cbuf = torch.zeros((75 * cpitch + coff,), dtype=torch.uint8, device="cuda")
+                    cview = cbuf[coff:coff + 75 * cpitch].view(75, cpitch)[:, :148]
+                    h, c = ldp.region_hist(view, k=3, regions=(3, 4), codes_out=cview)
+                    torch.cuda.synchronize()
+                    assert np.array_equal(c.cpu().numpy(), c_ref), (v, pitch, off, cpitch, coff)
+                    assert np.array_equal(_hist_np(h), h_ref)
+                    # bytes outside the code rectangle are untouched
+                    full = cbuf.cpu().numpy()
+                    inside = np.zeros_like(full, dtype=bool)
+                    for r in range(75):
+                        inside[coff + r * cpitch: coff + r * cpitch + 148] = True
+                    assert (full[~inside] == 0).all()
+            # an image whose buffer ends exactly at its last byte (no pitch padding on the last row)
+            H, W, P = 70, 133, 144
+            tight = torch.zeros((H - 1) * P + W, dtype=torch.uint8, device="cuda")
+            img2 = synth.image(12, H, W, 3.0)
+            rows = np.zeros((H, P), dtype=np.uint8)
+            rows[:, :W] = img2
+            tight.copy_(_dev(torch, rows.reshape(-1)[:(H - 1) * P + W]))
+            view2 = torch.as_strided(tight, (H, W), (P, 1))
+            h, c = ldp.region_hist(view2, k=3, regions=(2, 2))
             torch.cuda.synchronize()
-            assert np.array_equal(c.cpu().numpy(), c_ref), (pitch, off, cpitch, coff)
-            assert np.array_equal(_hist_np(h), h_ref)
-            # bytes outside the code rectangle are untouched
-            full = cbuf.cpu().numpy()
-            inside = np.zeros_like(full, dtype=bool)
-            for r in range(75):
-                inside[coff + r * cpitch: coff + r * cpitch + 148] = True
-            assert (full[~inside] == 0).all()
+            h_ref2, c_ref2 = oracle.extract(img2, k=3, R=2, C=2)
+            assert np.array_equal(c.cpu().numpy(), c_ref2) and np.array_equal(_hist_np(h), h_ref2), v
+    finally:
+        ldp.set_plain_variant(0)
 
 
 def test_many_small_regions_global_path(env):
