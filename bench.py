@@ -59,6 +59,7 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=1024, help="images in the oracle CPU sample")
     ap.add_argument("--no-extras", action="store_true", help="skip plain / LBP / serving / CPU legs")
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="measured seconds per serving rate")
+    ap.add_argument("--large", action="store_true", help="also time 64 images of 8192x8192, k = 1..4")
     return ap.parse_args()
 
 
@@ -153,6 +154,53 @@ def cpu_oracle_sample(n_images, H, W, k, threads=None):
                          compact=True, threads=threads, want_codes=True)
     dt = time.perf_counter() - t0
     return n_images * H * W / dt / 1e6, dt, threads
+
+
+def time_batch(ldp, torch, dev, Hs, Ws, seeds, ks, regions, sigma, steps, tune=True):
+    """Kernel-only and whole-step time of one batched plan per k over one
+    synthetic batch (the uneven and large-image legs)."""
+    import synth
+    from paper_1810_11518_gb300 import autotune
+
+    lay = ldp.BatchLayout.build(Hs, Ws, hist_len=regions[0] * regions[1] * 70)
+    host = torch.empty(lay.img_bytes, dtype=torch.uint8, pin_memory=True)
+    synth.batch_into(host.numpy(), seeds, lay.Hs, lay.Ws, lay.pitches, lay.img_off, sigma=sigma)
+    d_img = host.to(dev)
+    del host
+    d_codes = torch.empty(lay.code_bytes, dtype=torch.uint8, device=dev)
+    d_hist = torch.empty(lay.n * lay.hist_len, dtype=torch.int32, device=dev)
+    out = []
+    for k in ks:
+        hist_len = regions[0] * regions[1] * ldp.hist_bins(k)
+        descs = lay.descs(d_img.data_ptr(), d_codes.data_ptr())
+        descs["hist_offset"] = np.arange(lay.n, dtype=np.uint64) * np.uint64(hist_len)
+        d_desc = torch.from_numpy(descs.view(np.uint8)).to(dev)
+        d_count = torch.tensor([lay.n], dtype=torch.int32, device=dev)
+        with ldp.BatchPlan(lay.n, lay.pixels, k=k, regions=regions) as plan:
+            props = torch.cuda.get_device_properties(dev)
+            ent = autotune.lookup(torch.cuda.get_device_name(dev), props.multi_processor_count, "batch", k,
+                                  "hist+codes", lay.pixels / lay.n)
+            if ent:
+                plan.set_config(ent["variant"], ent["ctas_per_sm"])
+            elif tune:
+                autotune.tune_plan(plan, d_desc, d_count, d_hist, reps=3, warmup=1)
+            for _ in range(3):
+                plan.run(d_desc, d_count, d_hist)
+            plan.enable_timing(steps)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize(dev)
+            e0.record()
+            for _ in range(steps):
+                plan.run(d_desc, d_count, d_hist)
+            e1.record()
+            torch.cuda.synchronize(dev)
+            ms = e0.elapsed_time(e1) / steps
+            kms = statistics.mean(plan.kernel_times(steps))
+        alg = algorithmic_bytes(lay.Hs, lay.Ws, hist_len)
+        out.append({"images": lay.n, "pixels": lay.pixels, "k": k, "regions": list(regions),
+                    "ms_per_step": round(ms, 4), "value": round(lay.pixels / (ms * 1e-3) / 1e6, 3), "unit": UNIT,
+                    "kernel_ms": round(kms, 4), "achieved_gbs": round(alg / (kms * 1e-3) / 1e9, 1)})
+    return out
 
 
 def run_reference(a):
@@ -356,6 +404,16 @@ def main():
            "ms_per_step": round(ems, 4)}
 
     clk = clocks.stop()
+
+    if not a.no_extras and rank == 0:
+        # ---- uneven batch: 2048 images, H and W uniform on [64, 1024] ----
+        sizes = [synth.sizes(s, 64, 1024) for s in range(2048)]
+        extras["uneven_batched"] = time_batch(ldp, torch, dev, [h for h, _ in sizes], [w for _, w in sizes],
+                                              np.arange(2048), [k], (7, 6), 3.0, max(5, a.steps // 4))[0]
+    if a.large and rank == 0:
+        # ---- large images: 64 x 8192^2 (sigma 6), 16x16 regions, k = 1..4 ----
+        extras["large_batched"] = time_batch(ldp, torch, dev, [8192] * 64, [8192] * 64, np.arange(64), (1, 2, 3, 4),
+                                             (16, 16), 6.0, 5)
 
     if not a.no_extras and rank == 0 and a.serve_seconds > 0:
         # ---- continuous-batching serving (Poisson arrivals, uneven 64..1024 sizes) ----
