@@ -6,16 +6,19 @@
 // (ring p_0..p_7 counter-clockwise from East).  The eight S3_i and S8 are
 // built from column and row sums shared between neighbouring pixels.
 //
-// LDP arithmetic runs in FP32 on the FMA pipe and is exact: pixels enter as
-// 2048*b (b a byte), every sum is a multiple of 2048 below 2^23, and
-//     D_i = 2048*S3_i - 0.375*(2048*S8) = 256*m_i
-// is an integer multiple of 256 with |D_i| <= 979200.  The key
-//     key_i = (2^23 + 2^20 + 2^i) - |D_i|         (one FADD, |.| folded)
-// is an integer in [2^23, 2^24), so its float bit pattern is
-// 0x4B000000 + (2^20 + 2^i - |D_i|): bit patterns order like |m_i|
-// descending, ties go to the lower index (smaller 2^i), and the low byte is
-// the one-hot bit 2^i.  The k smallest keys are the k most outstanding
-// responses, and the low byte of the sum of their bit patterns IS the code.
+// LDP arithmetic is exact integer arithmetic on two pixels at once: every
+// 32-bit word holds two 16-bit lanes (pixel columns y and y+2), the sums are
+// plain 32-bit adds of such words and the selection is 16x2 SIMD min/max.
+// With p = S8 mod 2 (all m_i share the parity of S8) and C = 3824 + p,
+//     a_i = 8C - 8 m_i + i,   b_i = 8C + 8 m_i + i,   key_i = min(a_i, b_i)
+//         = 8 (C - |m_i|) + i
+// lies in [0, 30607]; a_i and b_i stay in [0, 61207], so neither ever leaves
+// its 16-bit lane, and the words are exact although intermediate terms may
+// carry between the lanes (everything before the min is linear mod 2^32).
+// Keys order like |m_i| descending with ties to the lower index, bits 0..2
+// hold i and bit 3 is 0 (C - |m_i| is even).  The k smallest keys are the k
+// most outstanding responses; a byte_perm with the keys' low bytes as its
+// selector turns each winner's index into the one-hot bit 2^i.
 #pragma once
 
 #include <cstdint>
@@ -25,7 +28,6 @@ namespace ldp {
 
 constexpr int kTileW = 128;           // output columns per tile: 32 lanes x 4 columns
 constexpr int kMaxSlots = 16;         // regions a tile may touch and still count in smem
-constexpr uint32_t kKeyBase = 1u << 20;  // > 256 * max|m_i| = 979200
 
 enum Mode { kLDP = 0, kLBP = 1 };
 
@@ -42,74 +44,70 @@ struct HistCfg {
     int R, C, nbins, compact;
 };
 
-__device__ __forceinline__ void cswap(uint32_t& a, uint32_t& b) {
-    uint32_t lo = min(a, b), hi = max(a, b);
-    a = lo;
-    b = hi;
+// 16x2 SIMD min / max of two words of 16-bit lanes.
+__device__ __forceinline__ uint32_t vmin2(uint32_t a, uint32_t b) {
+    uint32_t d;
+    asm("min.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+__device__ __forceinline__ uint32_t vmax2(uint32_t a, uint32_t b) {
+    uint32_t d;
+    asm("max.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
 }
 
-// Sum of the M smallest (SMALL) or M largest of eight distinct keys.
+// byte_perm with the hardware's full selector semantics: a selector nibble
+// with bit 3 set replicates the sign of the chosen byte.
+__device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
+    uint32_t d;
+    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(sel));
+    return d;
+}
+
+// The M best of eight keys per lane (SMALL: the M smallest, else the M
+// largest), unordered, in w[0..M-1].  Each half of four is reduced to its M
+// best in order; a bitonic half-cleaner then keeps the M best of both.
 template <int M, bool SMALL>
-__device__ __forceinline__ uint32_t sum_extreme(uint32_t (&k)[8]) {
-    if constexpr (!SMALL) {
-        // the M largest of k are the M smallest of ~k; ~(~a) = a restores them
-#pragma unroll
-        for (int i = 0; i < 8; ++i) k[i] = ~k[i];
-    }
-    uint32_t s;
-    if constexpr (M == 3) {
-        // sorted pairs -> three smallest of each half, sorted -> bitonic half-cleaner
-        cswap(k[0], k[1]);
-        cswap(k[2], k[3]);
-        cswap(k[4], k[5]);
-        cswap(k[6], k[7]);
-        uint32_t e0 = min(k[0], k[2]), ex = max(k[0], k[2]), ey = min(k[1], k[3]);
-        uint32_t e1 = min(ex, ey), e2 = max(ex, ey);
-        uint32_t f0 = min(k[4], k[6]), fx = max(k[4], k[6]), fy = min(k[5], k[7]);
-        uint32_t f1 = min(fx, fy), f2 = max(fx, fy);
-        uint32_t w0 = min(e0, f2), w1 = min(e1, f1), w2 = min(e2, f0);
-        s = SMALL ? w0 + w1 + w2 : (~w0) + (~w1) + (~w2);
-    } else if constexpr (M == 1) {
-        uint32_t a = min(min(k[0], k[1]), min(k[2], k[3]));
-        uint32_t b = min(min(k[4], k[5]), min(k[6], k[7]));
-        s = SMALL ? min(a, b) : ~min(a, b);
+__device__ __forceinline__ void select_best(const uint32_t (&k)[8], uint32_t (&w)[4]) {
+    auto lo = [](uint32_t a, uint32_t b) { return SMALL ? vmin2(a, b) : vmax2(a, b); };
+    auto hi = [](uint32_t a, uint32_t b) { return SMALL ? vmax2(a, b) : vmin2(a, b); };
+    if constexpr (M == 1) {
+        w[0] = lo(lo(lo(k[0], k[1]), lo(k[2], k[3])), lo(lo(k[4], k[5]), lo(k[6], k[7])));
     } else {
-        // Batcher odd-even merge sort of 8; unused comparator halves are
-        // removed by the compiler.
-        cswap(k[0], k[1]); cswap(k[2], k[3]); cswap(k[4], k[5]); cswap(k[6], k[7]);
-        cswap(k[0], k[2]); cswap(k[1], k[3]); cswap(k[4], k[6]); cswap(k[5], k[7]);
-        cswap(k[1], k[2]); cswap(k[5], k[6]);
-        cswap(k[0], k[4]); cswap(k[1], k[5]); cswap(k[2], k[6]); cswap(k[3], k[7]);
-        cswap(k[2], k[4]); cswap(k[3], k[5]);
-        cswap(k[1], k[2]); cswap(k[3], k[4]); cswap(k[5], k[6]);
-        s = 0;
+        uint32_t e[4], f[4];
+        auto half = [&](const uint32_t* x, uint32_t(&o)[4]) {
+            const uint32_t a0 = lo(x[0], x[1]), a1 = hi(x[0], x[1]);
+            const uint32_t a2 = lo(x[2], x[3]), a3 = hi(x[2], x[3]);
+            o[0] = lo(a0, a2);
+            const uint32_t ex = hi(a0, a2), ey = lo(a1, a3);
+            o[1] = lo(ex, ey);
+            o[2] = hi(ex, ey);
+            o[3] = hi(a1, a3);
+        };
+        half(k, e);
+        half(k + 4, f);
 #pragma unroll
-        for (int i = 0; i < M; ++i) s += SMALL ? k[i] : ~k[i];
+        for (int i = 0; i < M; ++i) w[i] = lo(e[i], f[M - 1 - i]);
     }
-    return s;
 }
 
-// LDP code from the eight keys: the k smallest keys win (for k >= 5 the
-// 8-k largest lose, which is the shorter network).
+// Codes of the two pixels of a pair of 16-bit lanes from their M best keys:
+// bytes 0 and 2 of the result (bytes 1 and 3 are don't-care).
 template <int K>
-__device__ __forceinline__ uint32_t select_code(uint32_t (&key)[8]) {
-    if constexpr (K <= 4) {
-        return sum_extreme<K, true>(key) & 0xFFu;
-    } else {
-        return (~sum_extreme<8 - K, false>(key)) & 0xFFu;
+__device__ __forceinline__ uint32_t code_pair(const uint32_t (&key)[8]) {
+    constexpr bool kSmall = K <= 4;
+    constexpr int M = kSmall ? K : 8 - K;
+    uint32_t w[4];
+    select_best<M, kSmall>(key, w);
+    uint32_t acc = 0;
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+        // selector nibble 0 = lane 0's index, nibble 2 = lane 1's (bit 3 of
+        // both is 0); the table bytes are 1, 2, 4, ..., 128
+        const uint32_t sel = prmt(w[j], 0u, 0x3120u);
+        acc |= prmt(0x08040201u, 0x80402010u, sel);
     }
-}
-
-// One image row restricted to the six columns v..v+5 a thread needs, as
-// exact floats 2048*b, with its pair sums h2[j] = x[j] + x[j+1] and triple
-// sums hs[t] = x[t] + x[t+1] + x[t+2].
-struct FRow {
-    float x[6], h2[5], hs[4];
-};
-
-__device__ __forceinline__ float byte_x2048(uint32_t w, uint32_t j) {
-    // bits 0x4B0000bb are the float 2^23 + b; 2048*(2^23 + b) - 2^34 = 2048*b exactly
-    return __fmaf_rn(__uint_as_float(__byte_perm(w, 0x4B000000u, 0x7650u | j)), 2048.0f, -17179869184.0f);
+    return kSmall ? acc : ~acc;  // for k >= 5 the M largest keys are the losers
 }
 
 // The six bytes v..v+5 of one image row a thread needs: w0 = bytes v..v+3,
@@ -133,15 +131,21 @@ __device__ __forceinline__ Raw load_raw(const uint8_t* __restrict__ row, int v, 
     return r;
 }
 
-__device__ __forceinline__ void unpack_frow(const Raw& w, FRow& r) {
-#pragma unroll
-    for (int j = 0; j < 4; ++j) r.x[j] = byte_x2048(w.w0, j);
-    r.x[4] = byte_x2048(w.w1, 0);
-    r.x[5] = byte_x2048(w.w1, 1);
-#pragma unroll
-    for (int j = 0; j < 5; ++j) r.h2[j] = r.x[j] + r.x[j + 1];
-#pragma unroll
-    for (int t = 0; t < 4; ++t) r.hs[t] = r.h2[t] + r.x[t + 2];
+// One image row restricted to the six columns v..v+5 a thread needs, in
+// pairs of 16-bit lanes: P[j] = (byte v+j, byte v+j+2), j = 0..3, and the row
+// three-sums T[c] = P[c] + P[c+1] + P[c+2], centred on columns v+1+c, v+3+c.
+struct SRow {
+    uint32_t P[4], T[2];
+};
+
+__device__ __forceinline__ void unpack_srow(const Raw& w, SRow& r) {
+    // source bytes 0..3 = columns v..v+3 (w0), 4..5 = v+4, v+5 (w1), 6..7 = 0
+    r.P[0] = __byte_perm(w.w0, w.w1, 0x6260u);
+    r.P[1] = __byte_perm(w.w0, w.w1, 0x6361u);
+    r.P[2] = __byte_perm(w.w0, w.w1, 0x6462u);
+    r.P[3] = __byte_perm(w.w0, w.w1, 0x6563u);
+    r.T[0] = r.P[0] + r.P[1] + r.P[2];
+    r.T[1] = r.P[1] + r.P[2] + r.P[3];
 }
 
 // LBP row in byte-SIMD form: s[d] holds bytes v+d..v+d+3 (d = 0, 1, 2), i.e.
@@ -181,35 +185,44 @@ __device__ __forceinline__ uint32_t lbp_row4(const BRow& A, const BRow& B, const
     return acc;
 }
 
-// Codes of the four pixels of one output row from rows A (x-1), B (x), C (x+1).
+// Codes of the two pixels of lane pair c (c = 0: columns v+1, v+3; c = 1:
+// columns v+2, v+4) of one output row, from rows A (x-1), B (x), C (x+1) and
+// the column three-sums V; bytes 0 and 2 of the result.
+template <int K, int c>
+__device__ __forceinline__ uint32_t ldp_pair(const SRow& A, const SRow& B, const SRow& C, const uint32_t (&V)[4]) {
+    constexpr int L = c, M = c + 1, R = c + 2;  // west, centre and east columns of the pair
+    const uint32_t S3[8] = {
+        V[R],                       // E : p7 + p0 + p1
+        B.P[R] + A.P[R] + A.P[M],   // NE: p0 + p1 + p2
+        A.T[c],                     // N : p1 + p2 + p3
+        A.P[M] + A.P[L] + B.P[L],   // NW: p2 + p3 + p4
+        V[L],                       // W : p3 + p4 + p5
+        B.P[L] + C.P[L] + C.P[M],   // SW: p4 + p5 + p6
+        C.T[c],                     // S : p5 + p6 + p7
+        C.P[M] + C.P[R] + B.P[R]};  // SE: p6 + p7 + p0
+    const uint32_t S8 = A.T[c] + C.T[c] + B.P[L] + B.P[R];
+    const uint32_t Q = (S8 & 0x00010001u) * 8u + 30592u * 0x00010001u;  // 8C per lane, C = 3824 + p
+    const uint32_t Za = Q + S8 * 24u, Zb = Q - S8 * 24u;               // 8C + 24 S8, 8C - 24 S8
+    uint32_t key[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const uint32_t ci = (uint32_t)i * 0x00010001u;
+        const uint32_t u = S3[i] * 64u + ci;  // 64 S3_i + i
+        const uint32_t a = Za - u + 2u * ci;  // 8C - 8 m_i + i
+        const uint32_t b = Zb + u;            // 8C + 8 m_i + i
+        key[i] = vmin2(a, b);
+    }
+    return code_pair<K>(key);
+}
+
+// Codes of the four pixels of one output row (byte t = column v+t).
 template <int K>
-__device__ __forceinline__ void ldp_row4(const FRow& A, const FRow& B, const FRow& C, uint32_t (&code)[4]) {
-    float PAC[6], V[6];
+__device__ __forceinline__ uint32_t ldp_row4(const SRow& A, const SRow& B, const SRow& C) {
+    uint32_t V[4];  // column three-sums
 #pragma unroll
-    for (int j = 0; j < 6; ++j) {
-        PAC[j] = A.x[j] + C.x[j];  // column j: top + bottom
-        V[j] = PAC[j] + B.x[j];    // column j: vertical three-sum
-    }
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-        // -0.375 * 2048*S8 = -768*S8, with S8 = V[t] + V[t+2] + A[t+1] + C[t+1]
-        const float nb = ((V[t] + V[t + 2]) + PAC[t + 1]) * -0.375f;
-        const float bn0 = B.x[t] + nb, bn2 = B.x[t + 2] + nb;
-        float D[8];
-        D[0] = V[t + 2] + nb;      // E : p7 + p0 + p1
-        D[1] = A.h2[t + 1] + bn2;  // NE: p0 + p1 + p2
-        D[2] = A.hs[t] + nb;       // N : p1 + p2 + p3
-        D[3] = A.h2[t] + bn0;      // NW: p2 + p3 + p4
-        D[4] = V[t] + nb;          // W : p3 + p4 + p5
-        D[5] = C.h2[t] + bn0;      // SW: p4 + p5 + p6
-        D[6] = C.hs[t] + nb;       // S : p5 + p6 + p7
-        D[7] = C.h2[t + 1] + bn2;  // SE: p6 + p7 + p0
-        uint32_t key[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i)
-            key[i] = __float_as_uint((8388608.0f + 1048576.0f + (float)(1 << i)) - fabsf(D[i]));
-        code[t] = select_code<K>(key);
-    }
+    for (int j = 0; j < 4; ++j) V[j] = A.P[j] + B.P[j] + C.P[j];
+    const uint32_t c02 = ldp_pair<K, 0>(A, B, C, V), c13 = ldp_pair<K, 1>(A, B, C, V);
+    return __byte_perm(c02, c13, 0x6240u);
 }
 
 // Band b of nb bands over n pixels covers [floor(b*n/nb), floor((b+1)*n/nb));
@@ -391,13 +404,21 @@ __device__ __forceinline__ void warp_tile(const Job& jb, const HistCfg& hc, int 
     }
     // region row of image row x = u + 1, advanced as the rows go down
     int ri = ri_lo, next_b = 0, rowb = 0;
+    // shared-memory byte address of bin 0 of each column's current slot
+    uint32_t sbase[4] = {0u, 0u, 0u, 0u};
+    const uint32_t wh_addr = HIST && use_smem ? smem_addr(wh) : 0u;
+    auto set_sbase = [&]() {
+#pragma unroll
+        for (int t = 0; t < 4; ++t) sbase[t] = wh_addr + 4u * (uint32_t)(rowb + colb[t]);
+    };
     if constexpr (HIST) {
         next_b = band_lo(ri + 1, H, hc.R);
         rowb = use_smem ? 0 : ri * hc.C;
+        if (use_smem) set_sbase();
     }
 
-    // codes of output row u -> code map and histogram
-    auto emit = [&](int u, const uint32_t (&code)[4], uint32_t packed) {
+    // codes of output row u (byte t of `packed` = column v+t) -> code map and histogram
+    auto emit = [&](int u, uint32_t packed) {
         if (jb.codes) {
             uint8_t* cp = jb.codes + (size_t)u * (size_t)jb.Pc + v;
             if (fast_st) {
@@ -405,7 +426,7 @@ __device__ __forceinline__ void warp_tile(const Job& jb, const HistCfg& hc, int 
             } else {
 #pragma unroll
                 for (int t = 0; t < 4; ++t)
-                    if (valid[t]) cp[t] = (uint8_t)code[t];
+                    if (valid[t]) cp[t] = (uint8_t)(packed >> (8 * t));
             }
         }
         if constexpr (HIST) {
@@ -413,36 +434,37 @@ __device__ __forceinline__ void warp_tile(const Job& jb, const HistCfg& hc, int 
                 ++ri;
                 next_b = band_lo(ri + 1, H, hc.R);
                 rowb = use_smem ? (ri - ri_lo) * ncs * 256 : ri * hc.C;
+                if (use_smem) set_sbase();
             }
             if (use_smem) {
 #pragma unroll
                 for (int t = 0; t < 4; ++t)
-                    if (valid[t]) atomicAdd(&wh[rowb + colb[t] + (int)code[t]], 1u);
+                    if (valid[t]) {
+                        const uint32_t code = prmt(packed, 0u, 0x4440u | (uint32_t)t);
+                        uint32_t addr;
+                        asm("mad.lo.u32 %0, %1, 4, %2;" : "=r"(addr) : "r"(code), "r"(sbase[t]));
+                        asm volatile("red.shared.add.u32 [%0], 1;" ::"r"(addr) : "memory");
+                    }
             } else {
 #pragma unroll
                 for (int t = 0; t < 4; ++t)
-                    if (valid[t])
-                        atomicAdd(&jb.hist[(size_t)(rowb + colb[t]) * hc.nbins + bin_of((int)code[t], hc, K)], 1u);
+                    if (valid[t]) {
+                        const int code = (int)((packed >> (8 * t)) & 0xFFu);
+                        atomicAdd(&jb.hist[(size_t)(rowb + colb[t]) * hc.nbins + bin_of(code, hc, K)], 1u);
+                    }
             }
         }
     };
-    auto codes_of_row = [&](const auto& A, const auto& B, const auto& C, uint32_t (&code)[4]) -> uint32_t {
-        if constexpr (MODE == kLDP) {
-            ldp_row4<K>(A, B, C, code);
-            const uint32_t p01 = __byte_perm(code[0], code[1], 0x0040u);
-            const uint32_t p23 = __byte_perm(code[2], code[3], 0x0040u);
-            return __byte_perm(p01, p23, 0x5410u);
-        } else {
-            const uint32_t packed = lbp_row4(A, B, C);
-#pragma unroll
-            for (int t = 0; t < 4; ++t) code[t] = (packed >> (8 * t)) & 0xFFu;
-            return packed;
-        }
+    auto codes_of_row = [&](const auto& A, const auto& B, const auto& C) -> uint32_t {
+        if constexpr (MODE == kLDP)
+            return ldp_row4<K>(A, B, C);
+        else
+            return lbp_row4(A, B, C);
     };
-    using Row = std::conditional_t<MODE == kLDP, FRow, BRow>;
+    using Row = std::conditional_t<MODE == kLDP, SRow, BRow>;
     auto unpack = [&](const Raw& w, Row& r) {
         if constexpr (MODE == kLDP)
-            unpack_frow(w, r);
+            unpack_srow(w, r);
         else
             unpack_brow(w, r);
     };
@@ -511,9 +533,7 @@ __device__ __forceinline__ void warp_tile(const Job& jb, const HistCfg& hc, int 
             if (!ok) return;
             unpack(read(ir), C);
             if (ir % kStageRows == kStageRows - 1) fill(ir / kStageRows + kStages);  // stage fully read
-            uint32_t code[4];
-            const uint32_t packed = codes_of_row(A, B, C, code);
-            emit(u0 + ou, code, packed);
+            emit(u0 + ou, codes_of_row(A, B, C));
         };
         const int nout = ue - u0;
         int ou = 0;
@@ -547,9 +567,7 @@ __device__ __forceinline__ void warp_tile(const Job& jb, const HistCfg& hc, int 
             unpack(nx, C);
             if (u + 1 < ue) nx = load_raw(pf, v, W, fast_ld);
             pf += P;
-            uint32_t code[4];
-            const uint32_t packed = codes_of_row(A, B, C, code);
-            emit(u, code, packed);
+            emit(u, codes_of_row(A, B, C));
         };
         int u = u0;
         for (; u + 3 <= ue; u += 3) {
