@@ -10,9 +10,9 @@
 // 32-bit word holds two 16-bit lanes (pixel columns y and y+2), the sums are
 // plain 32-bit adds of such words and the selection is 16x2 SIMD min/max.
 // With p = S8 mod 2 (all m_i share the parity of S8) and C = 3824 + p,
-//     a_i = 8C - 8 m_i + i,   b_i = 8C + 8 m_i + i,   key_i = min(a_i, b_i)
+//     a_i = 8C - 8 m_i,   b_i = 8C + 8 m_i,   key_i = min(a_i, b_i) + i
 //         = 8 (C - |m_i|) + i
-// lies in [0, 30607]; a_i and b_i stay in [0, 61207], so neither ever leaves
+// lies in [0, 30607]; a_i and b_i stay in [0, 61200], so neither ever leaves
 // its 16-bit lane, and the words are exact although intermediate terms may
 // carry between the lanes (everything before the min is linear mod 2^32).
 // Keys order like |m_i| descending with ties to the lower index, bits 0..2
@@ -206,11 +206,12 @@ __device__ __forceinline__ uint32_t ldp_pair(const SRow& A, const SRow& B, const
     uint32_t key[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-        const uint32_t ci = (uint32_t)i * 0x00010001u;
-        const uint32_t u = S3[i] * 64u + ci;  // 64 S3_i + i
-        const uint32_t a = Za - u + 2u * ci;  // 8C - 8 m_i + i
-        const uint32_t b = Zb + u;            // 8C + 8 m_i + i
-        key[i] = vmin2(a, b);
+        // a = 8C - 8 m_i, b = 8C + 8 m_i: one multiply-add each (FMA pipe),
+        // the min and the tie index i on the ALU
+        uint32_t a, b;
+        asm("mad.lo.u32 %0, %1, -64, %2;" : "=r"(a) : "r"(S3[i]), "r"(Za));
+        asm("mad.lo.u32 %0, %1, 64, %2;" : "=r"(b) : "r"(S3[i]), "r"(Zb));
+        key[i] = vmin2(a, b) + (uint32_t)i * 0x00010001u;
     }
     return code_pair<K>(key);
 }
