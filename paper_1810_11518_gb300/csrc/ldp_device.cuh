@@ -407,7 +407,7 @@ __device__ __forceinline__ void warp_tile(const Job& jb, const HistCfg& hc, int 
     int ri = ri_lo, next_b = 0, rowb = 0;
     // shared-memory byte address of bin 0 of each column's current slot
     uint32_t sbase[4] = {0u, 0u, 0u, 0u};
-    const uint32_t wh_addr = HIST && use_smem ? smem_addr(wh) : 0u;
+    const uint32_t wh_addr = HIST && use_smem && MODE == kLDP ? smem_addr(wh) : 0u;
     auto set_sbase = [&]() {
 #pragma unroll
         for (int t = 0; t < 4; ++t) sbase[t] = wh_addr + 4u * (uint32_t)(rowb + colb[t]);
@@ -415,7 +415,7 @@ __device__ __forceinline__ void warp_tile(const Job& jb, const HistCfg& hc, int 
     if constexpr (HIST) {
         next_b = band_lo(ri + 1, H, hc.R);
         rowb = use_smem ? 0 : ri * hc.C;
-        if (use_smem) set_sbase();
+        if (use_smem && MODE == kLDP) set_sbase();
     }
 
     // codes of output row u (byte t of `packed` = column v+t) -> code map and histogram
@@ -435,9 +435,11 @@ __device__ __forceinline__ void warp_tile(const Job& jb, const HistCfg& hc, int 
                 ++ri;
                 next_b = band_lo(ri + 1, H, hc.R);
                 rowb = use_smem ? (ri - ri_lo) * ncs * 256 : ri * hc.C;
-                if (use_smem) set_sbase();
+                if (use_smem && MODE == kLDP) set_sbase();
             }
-            if (use_smem) {
+            if (use_smem && MODE == kLDP) {
+                // LDP codes spread over the bins: one byte extract, one
+                // multiply-add for the address, one reduction per pixel
 #pragma unroll
                 for (int t = 0; t < 4; ++t)
                     if (valid[t]) {
@@ -446,6 +448,12 @@ __device__ __forceinline__ void warp_tile(const Job& jb, const HistCfg& hc, int 
                         asm("mad.lo.u32 %0, %1, 4, %2;" : "=r"(addr) : "r"(code), "r"(sbase[t]));
                         asm volatile("red.shared.add.u32 [%0], 1;" ::"r"(addr) : "memory");
                     }
+            } else if (use_smem) {
+                // LBP: neighbouring lanes often share a code (flat areas give
+                // 255); the compiler's shared atomicAdd is faster there
+#pragma unroll
+                for (int t = 0; t < 4; ++t)
+                    if (valid[t]) atomicAdd(&wh[rowb + colb[t] + (int)((packed >> (8 * t)) & 0xFFu)], 1u);
             } else {
 #pragma unroll
                 for (int t = 0; t < 4; ++t)
