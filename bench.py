@@ -27,6 +27,7 @@ from __future__ import annotations
 
 import argparse
 import ctypes
+import hashlib
 import json
 import os
 import statistics
@@ -68,6 +69,26 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+# DRAM bytes (read + write) per input pixel of the persistent LDP kernel,
+# from one ncu capture of 512 x 640x490 images (k=3, 7x6 regions; summary in
+# profiles/k_batch_ldp_k3_512img_full.md), scaled to a launch by its pixels.
+# Valid only for the kernel sources it was taken on: any change to them
+# reports traffic as null until a new capture is recorded here.
+TRAFFIC_PER_PX = 301.27e6 / (512 * 640 * 490)
+TRAFFIC_SOURCES = ("paper_1810_11518_gb300/csrc/ldp_device.cuh", "paper_1810_11518_gb300/csrc/ldp_kernels.cu")
+TRAFFIC_SHA256 = "280a6ea11ab325ab444a25528e5ed73d1c9f78c5f90d79f27f64c8da99fe98db"
+
+
+def measured_traffic(pixels, k, H, W):
+    if (k, H, W) != (3, 490, 640):
+        return None
+    h = hashlib.sha256()
+    for f in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return int(round(TRAFFIC_PER_PX * pixels)) if h.hexdigest() == TRAFFIC_SHA256 else None
 
 
 def algorithmic_bytes(Hs, Ws, hist_len):
@@ -447,14 +468,15 @@ def main():
                                    f"codes + 7x6 region histograms ({nb} bins), batched persistent graph launch",
                        "images": n, "height": H, "width": W, "k": k, "regions": [7, 6],
                        "variant": ldp.variant_name(variant), "ctas_per_sm": cps,
-                       "autotuned": tuned, "l2": "inputs+outputs 2.6 GB >> 129 MB L2, no flush",
+                       "autotuned": tuned, "l2": f"inputs+outputs {alg_bytes / 1e9:.2f} GB >> 129 MB L2, no flush",
                        "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "achieved": round(achieved_gbs, 1), "peak": peak, "unit": "GB/s",
-                         "frac": round(achieved_gbs / peak, 4), "traffic": None,
+                         "frac": round(achieved_gbs / peak, 4),
+                         "traffic": measured_traffic(n * H * W, k, H, W),
                          "kernel": "k_batch (persistent LDP codes + region hist)",
                          "kernel_ms": round(k_ms, 4), "algorithmic_bytes_per_launch": alg_bytes,
                          "peak_source": f"{peak_src} hbm_gbs",
-                         "binding_roof": "instruction issue (integer + FP32 per-pixel work); see profiles/"},
+                         "binding_roof": "integer pipes and issue (ALU 73%, issue 81% in ncu); see profiles/"},
             "e2e": e2e,
             "gpu_launches": 3 * a.steps,
             "clocks": clk,
