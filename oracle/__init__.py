@@ -65,6 +65,8 @@ def _load():
             lib.oracle_extract_batch.argtypes = [i32, vp, i64p, vp, vp, vp, i32, i32, i32, i32, i32,
                                                  vp, i64p, vp, i64p, vp, i32]
             lib.aldp_codes.argtypes = [vp, i32, i32, i32, i32, vp, i32]
+            lib.oracle_window_count.argtypes = [i32, i32, i32]
+            lib.oracle_window_hist.argtypes = [vp, i32, i32, i32, i32, i32, i32, i32, i32, vp]
             _lib = lib
     return _lib
 
@@ -185,6 +187,38 @@ def region_hist(code_map, H, W, R, C, nbins_k) -> np.ndarray:
     if rc:
         raise ValueError("oracle_region_hist rejected the arguments")
     return out
+
+
+def window_count(n: int, w: int, s: int) -> int:
+    """Windows of size w at stride s along an axis of n pixels (Sec. 3.2)."""
+    c = _load().oracle_window_count(n, w, s)
+    if c < 0:
+        raise ValueError("window size and stride must be positive")
+    return c
+
+
+def window_hist(code_map, H, W, wh, ww, sh, sw, nbins_k) -> np.ndarray:
+    """Sliding-window histograms from a full interior code map of shape (H-2, W-2):
+    shape (window rows, window columns, nbins)."""
+    code_map = np.ascontiguousarray(code_map, dtype=np.uint8)
+    nb = len(compact_codes(nbins_k)) if nbins_k else 256
+    out = np.zeros((window_count(H, wh, sh), window_count(W, ww, sw), nb), dtype=np.uint32)
+    rc = _load().oracle_window_hist(code_map.ctypes.data, H, W, code_map.shape[1], wh, ww, sh, sw, nbins_k,
+                                    out.ctypes.data)
+    if rc:
+        raise ValueError("oracle_window_hist rejected the arguments")
+    return out
+
+
+def extract_windows(img, k: int = 3, window=(20, 20), stride=None, compact: bool = True,
+                    mode: int = MODE_LDP):
+    """(window histograms, codes) for one image; stride defaults to the window size."""
+    img = _u8(img)
+    H, W = img.shape
+    stride = tuple(window) if stride is None else tuple(stride)
+    cm = codes(img, k=k, mode=mode)
+    nbk = k if (mode == MODE_LDP and compact) else 0
+    return window_hist(cm, H, W, window[0], window[1], stride[0], stride[1], nbk), cm
 
 
 def extract(img, k: int = 3, R: int = 1, C: int = 1, compact: bool = True, mode: int = MODE_LDP,

@@ -165,6 +165,42 @@ int oracle_region_hist(const uint8_t *codes, int H, int W, int code_pitch, int R
     return 0;
 }
 
+int oracle_window_count(int n, int w, int s) {
+    if (w < 1 || s < 1 || n < 0) return -1;
+    if (n <= w) return 1;
+    return (n - w + s - 1) / s + 1;
+}
+
+int oracle_window_hist(const uint8_t *codes, int H, int W, int code_pitch, int wh, int ww, int sh,
+                       int sw, int nbins_k, uint32_t *hist) {
+    if (!codes || !hist || H < 3 || W < 3 || nbins_k < 0 || nbins_k > 7) return -1;
+    int nr = oracle_window_count(H, wh, sh), nc = oracle_window_count(W, ww, sw);
+    if (nr < 1 || nc < 1) return -1;
+    int nbins = nbins_k ? oracle_compact_codes(nbins_k, NULL) : 256;
+    int bin_of[256];
+    for (int v = 0; v < 256; ++v) bin_of[v] = nbins_k ? oracle_bin_of_code(v, nbins_k) : v;
+    memset(hist, 0, sizeof(uint32_t) * (size_t)nr * (size_t)nc * (size_t)nbins);
+    for (int a = 0; a < nr; ++a) {
+        int xlo = a * sh, xhi = a * sh + wh;
+        if (xhi > H) xhi = H;
+        if (xlo < 1) xlo = 1;
+        if (xhi > H - 1) xhi = H - 1;
+        for (int b = 0; b < nc; ++b) {
+            int ylo = b * sw, yhi = b * sw + ww;
+            if (yhi > W) yhi = W;
+            if (ylo < 1) ylo = 1;
+            if (yhi > W - 1) yhi = W - 1;
+            uint32_t *h = hist + ((size_t)a * nc + b) * (size_t)nbins;
+            for (int x = xlo; x < xhi; ++x)
+                for (int y = ylo; y < yhi; ++y) {
+                    int bin = bin_of[codes[(size_t)(x - 1) * code_pitch + (size_t)(y - 1)]];
+                    if (bin >= 0) h[bin] += 1;
+                }
+        }
+    }
+    return 0;
+}
+
 int oracle_extract(const uint8_t *img, int H, int W, int pitch, int mode, int k, int R, int C,
                    int compact, uint32_t *hist, uint8_t *codes, int code_pitch) {
     if (!img || H < 3 || W < 3 || pitch < W) return -1;

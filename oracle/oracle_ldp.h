@@ -26,6 +26,9 @@
  *     coordinates; region (ri, rj) is stored at (ri*C + rj) * nbins.
  *   - LBP: bit j is set when neighbour p_j >= centre, p_0..p_7 taken
  *     counter-clockwise from East like the masks.
+ *   - Sliding windows (Sec. 3.2): windows start at multiples of the stride
+ *     and are clipped at the image edge; with stride = size this reproduces
+ *     every window count of Table 3 for a 280-pixel side.
  * All counters are uint32.
  */
 #ifndef ORACLE_LDP_H
@@ -69,6 +72,20 @@ void oracle_band(int n, int nb, int b, int *lo, int *hi);
  * 1..7: compact C(8,k) bins.  hist is overwritten (R*C*nbins uint32). */
 int oracle_region_hist(const uint8_t *codes, int H, int W, int code_pitch, int R, int C,
                        int nbins_k, uint32_t *hist);
+
+/* Sliding windows along one axis of n pixels (Sec. 3.2, Table 3): window j
+ * of size w at stride s covers [j*s, min(j*s + w, n)); there are 1 window
+ * when n <= w, else ceil((n - w) / s) + 1 (the last one is clipped to n).
+ * Returns -1 for w < 1 or s < 1. */
+int oracle_window_count(int n, int w, int s);
+
+/* Window histograms from a full interior code map (as oracle_region_hist):
+ * window (a, b) covers image rows [a*sh, min(a*sh + wh, H)) and columns
+ * [b*sw, min(b*sw + ww, W)), intersected with the interior, and is stored at
+ * (a * nwc + b) * nbins with nwc = oracle_window_count(W, ww, sw).  hist is
+ * overwritten. */
+int oracle_window_hist(const uint8_t *codes, int H, int W, int code_pitch, int wh, int ww, int sh,
+                       int sw, int nbins_k, uint32_t *hist);
 
 /* Whole path for one image: codes (optional, may be NULL) + region hists.
  * mode 0 = LDP(k), 1 = LBP; compact selects C(8,k) bins (LDP only). */
