@@ -113,6 +113,61 @@ LDP_API int lbp_codes(const uint8_t *d_img, int H, int W, int pitch, uint8_t *d_
 LDP_API int lbp_region_hist(const uint8_t *d_img, int H, int W, int pitch, int R, int C, uint32_t *d_hist,
                     uint8_t *d_codes_or_null, int code_pitch, void *stream);
 
+/* ---- sliding windows (Sec. 3.2, Table 3) ---- */
+
+/* Windows of wh x ww pixels whose origins step by (sh, sw): window (a, b)
+ * covers image rows [a*sh, min(a*sh + wh, H)) and columns
+ * [b*sw, min(b*sw + ww, W)), interior pixels only (windows overlap when the
+ * stride is below the size, leave gaps when above).  compact as in
+ * ldp_region_spec.  All five fields >= 1 except compact (0 or 1). */
+typedef struct {
+    int32_t wh, ww;
+    int32_t sh, sw;
+    int32_t compact;
+} ldp_window_spec;
+
+/* Windows along one axis of n pixels: 1 when n <= w, else
+ * ceil((n - w) / s) + 1 (the last one clipped at n).  -1 when w < 1 or
+ * s < 1.  With s = w this is ceil(n / w): Table 3's counts for n = 280. */
+LDP_API int ldp_window_count(int n, int w, int s);
+
+/* Device scratch bytes ldp_window_hist / lbp_window_hist need for an H x W
+ * image (k = 0: LBP or raw bins): a code map of (H-2) x (W-2) bytes unless
+ * codes_given, plus the cell histograms when the windows overlap or leave
+ * gaps (cells of gcd(size, stride) pixels).  0 on invalid arguments. */
+LDP_API uint64_t ldp_window_scratch_bytes(int H, int W, int k, ldp_window_spec ws, int codes_given);
+
+/* LDP codes of one image (Eq. 1-3), then the histogram of every sliding
+ * window (Eq. 4-6 per window, Sec. 3.2) into d_hist: nwr x nwc x nbins
+ * uint32 (every element written), nwr = ldp_window_count(H, wh, sh),
+ * nwc = ldp_window_count(W, ww, sw).  Codes go to d_codes_or_null
+ * (code_pitch) or to the scratch.  d_scratch: at least
+ * ldp_window_scratch_bytes(H, W, k, ws, d_codes_or_null != NULL) bytes,
+ * 256-byte aligned, owned by the caller (NULL when that is 0).  EINVAL as
+ * ldp_region_hist, plus a bad window spec or short scratch. */
+LDP_API int ldp_window_hist(const uint8_t *d_img, int H, int W, int pitch, int k, ldp_window_spec ws,
+                            uint32_t *d_hist, uint8_t *d_codes_or_null, int code_pitch, void *d_scratch,
+                            uint64_t scratch_bytes, void *stream);
+
+/* The same with LBP codes (Sec. 2.1) and 256 raw bins (ws.compact must be 0). */
+LDP_API int lbp_window_hist(const uint8_t *d_img, int H, int W, int pitch, ldp_window_spec ws, uint32_t *d_hist,
+                            uint8_t *d_codes_or_null, int code_pitch, void *d_scratch, uint64_t scratch_bytes,
+                            void *stream);
+
+/* Scratch bytes of ldp_batch_window_hist: count x (cell words of a
+ * max_H x max_W image) x 4, or 0 when stride = size. */
+LDP_API uint64_t ldp_batch_window_scratch_bytes(int count, int max_H, int max_W, int k, ldp_window_spec ws);
+
+/* Window histograms of `count` images (host value) from code maps already
+ * in device memory, e.g. stored by ldp_batch_run: image i is d_descs[i]
+ * (codes, code_pitch, H, W; img unused), its windows go to
+ * d_hist + hist_offset.  Every image must satisfy H <= max_H, W <= max_W;
+ * images with codes == NULL are skipped.  k >= 1 with ws.compact = 1:
+ * C(8,k) bins; else 256 raw bins (k = 0 for LBP maps). */
+LDP_API int ldp_batch_window_hist(const ldp_image_desc *d_descs, int count, int max_H, int max_W, int k,
+                                  ldp_window_spec ws, uint32_t *d_hist, void *d_scratch, uint64_t scratch_bytes,
+                                  void *stream);
+
 /* ---- batches of images of any sizes: one persistent launch ---- */
 
 typedef struct ldp_batch_plan ldp_batch_plan;

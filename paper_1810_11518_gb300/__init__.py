@@ -18,11 +18,12 @@ from math import comb
 import numpy as np
 
 from . import _abi
-from ._abi import LdpError, RegionSpec
+from ._abi import LdpError, RegionSpec, WindowSpec
 
 __all__ = ["codes", "region_hist", "lbp_codes", "lbp_region_hist", "hist_bins", "bin_of_code",
            "BatchPlan", "BatchLayout", "DESC_DTYPE", "LdpError", "device_status", "num_variants",
-           "variant_name", "set_plain_variant", "load", "batch_run_noalloc"]
+           "variant_name", "set_plain_variant", "load", "batch_run_noalloc", "window_count", "window_hist",
+           "lbp_window_hist", "batch_window_hist"]
 
 DESC_DTYPE = np.dtype([("img", "<u8"), ("H", "<i4"), ("W", "<i4"), ("pitch", "<i4"),
                        ("code_pitch", "<i4"), ("codes", "<u8"), ("hist_offset", "<u8")])
@@ -128,6 +129,76 @@ def lbp_region_hist(img, regions=(1, 1), with_codes: bool = True, hist=None, cod
         cptr = ctypes.c_void_p(out.data_ptr())
     _abi.call("lbp_region_hist", p, H, W, P, R, C, ctypes.c_void_p(hist.data_ptr()), cptr, pc, _stream(stream))
     return hist, out
+
+
+def window_count(n: int, w: int, s: int) -> int:
+    """Sliding windows of size w at stride s along an axis of n pixels (Sec. 3.2)."""
+    c = int(_abi.load().ldp_window_count(n, w, s))
+    if c < 0:
+        raise ValueError("window size and stride must be positive")
+    return c
+
+
+def _window_run(fn, img, k, window, stride, compact, with_codes, hist, codes_out, stream):
+    torch = _torch()
+    p, H, W, P = _img(img)
+    wh, ww = window
+    sh, sw = (wh, ww) if stride is None else stride
+    ws = WindowSpec(wh, ww, sh, sw, int(compact))
+    nb = comb(8, k) if compact else 256
+    shape = (window_count(H, wh, sh), window_count(W, ww, sw), nb)
+    if hist is None:
+        hist = torch.empty(shape, dtype=torch.int32, device=img.device)
+    elif hist.numel() != shape[0] * shape[1] * nb or not hist.is_contiguous():
+        raise ValueError(f"hist must be a contiguous int32 tensor of {shape[0] * shape[1] * nb} elements")
+    cptr, pc, out = None, 0, None
+    if with_codes:
+        out, pc = _alloc_codes(img, H, W, codes_out)
+        cptr = ctypes.c_void_p(out.data_ptr())
+    need = int(_abi.load().ldp_window_scratch_bytes(H, W, k if fn == "ldp_window_hist" else 0, ws,
+                                                    int(with_codes)))
+    scratch = torch.empty(max(need, 1), dtype=torch.uint8, device=img.device) if need else None
+    sptr = ctypes.c_void_p(scratch.data_ptr()) if scratch is not None else None
+    args = [p, H, W, P] + ([k] if fn == "ldp_window_hist" else []) + [
+        ws, ctypes.c_void_p(hist.data_ptr()), cptr, pc, sptr, need, _stream(stream)]
+    _abi.call(fn, *args)
+    if scratch is not None:  # keep the scratch alive until the kernels have read it
+        scratch.record_stream(torch.cuda.current_stream() if stream is None else stream)
+    return hist, out
+
+
+def window_hist(img, k: int = 3, window=(20, 20), stride=None, compact: bool = True, with_codes: bool = True,
+                hist=None, codes_out=None, stream=None):
+    """LDP codes + sliding-window histograms (Sec. 3.2): windows of window = (wh, ww)
+    pixels whose origins step by stride (default: the window size).
+
+    Returns (hist int32 tensor (window rows, window cols, nbins) of uint32 counts, codes or None)."""
+    return _window_run("ldp_window_hist", img, k, window, stride, compact, with_codes, hist, codes_out, stream)
+
+
+def lbp_window_hist(img, window=(20, 20), stride=None, with_codes: bool = True, hist=None, codes_out=None,
+                    stream=None):
+    """LBP codes + 256-bin sliding-window histograms."""
+    return _window_run("lbp_window_hist", img, 0, window, stride, False, with_codes, hist, codes_out, stream)
+
+
+def batch_window_hist(d_descs, count: int, max_hw, k: int, window, stride=None, compact: bool = True,
+                      hist=None, stream=None):
+    """Window histograms of `count` code maps already in device memory (descriptors
+    `d_descs`, a CUDA tensor of DESC_DTYPE records; windows of image i at
+    hist + hist_offset).  k = 0: raw 256 bins (LBP maps)."""
+    torch = _torch()
+    wh, ww = window
+    sh, sw = (wh, ww) if stride is None else stride
+    ws = WindowSpec(wh, ww, sh, sw, int(compact))
+    need = int(_abi.load().ldp_batch_window_scratch_bytes(count, max_hw[0], max_hw[1], k, ws))
+    scratch = torch.empty(need, dtype=torch.uint8, device=hist.device) if need else None
+    _abi.call("ldp_batch_window_hist", ctypes.c_void_p(d_descs.data_ptr()), count, max_hw[0], max_hw[1], k, ws,
+              ctypes.c_void_p(hist.data_ptr()), ctypes.c_void_p(scratch.data_ptr()) if scratch is not None else None,
+              need, _stream(stream))
+    if scratch is not None:
+        scratch.record_stream(torch.cuda.current_stream() if stream is None else stream)
+    return hist
 
 
 def num_variants() -> int:

@@ -27,6 +27,8 @@ EXPORTS = [
     "ldp_hist_bins", "ldp_bin_of_code", "ldp_last_error", "ldp_device_status", "ldp_version",
     "ldp_batch_plan_enable_timing", "ldp_batch_plan_kernel_times", "ldp_batch_run_noalloc",
     "ldp_server_create", "ldp_server_submit", "ldp_server_poll", "ldp_server_stats", "ldp_server_destroy",
+    "ldp_window_count", "ldp_window_scratch_bytes", "ldp_window_hist", "lbp_window_hist",
+    "ldp_batch_window_scratch_bytes", "ldp_batch_window_hist",
 ]
 
 
@@ -38,6 +40,11 @@ class LdpError(RuntimeError):
 
 class RegionSpec(ctypes.Structure):
     _fields_ = [("R", ctypes.c_int32), ("C", ctypes.c_int32), ("compact", ctypes.c_int32)]
+
+
+class WindowSpec(ctypes.Structure):
+    _fields_ = [("wh", ctypes.c_int32), ("ww", ctypes.c_int32), ("sh", ctypes.c_int32), ("sw", ctypes.c_int32),
+                ("compact", ctypes.c_int32)]
 
 
 class ImageDesc(ctypes.Structure):
@@ -106,11 +113,19 @@ def load(path: str | None = None):
             "ldp_server_poll": [vp, ctypes.POINTER(Completion), i32, ctypes.POINTER(i32)],
             "ldp_server_stats": [vp, ctypes.POINTER(ServerStats)],
             "ldp_server_destroy": [vp],
+            "ldp_window_count": [i32, i32, i32],
+            "ldp_window_scratch_bytes": [i32, i32, i32, WindowSpec, i32],
+            "ldp_window_hist": [vp, i32, i32, i32, i32, WindowSpec, vp, vp, i32, vp, u64, vp],
+            "lbp_window_hist": [vp, i32, i32, i32, WindowSpec, vp, vp, i32, vp, u64, vp],
+            "ldp_batch_window_scratch_bytes": [i32, i32, i32, i32, WindowSpec],
+            "ldp_batch_window_hist": [vp, i32, i32, i32, i32, WindowSpec, vp, vp, u64, vp],
         }
         for name, args in sig.items():
             fn = getattr(lib, name)
             fn.argtypes = args
             fn.restype = ctypes.c_int
+        lib.ldp_window_scratch_bytes.restype = u64
+        lib.ldp_batch_window_scratch_bytes.restype = u64
         lib.ldp_last_error.restype = ctypes.c_char_p
         lib.ldp_variant_name.restype = ctypes.c_char_p
         _lib = lib

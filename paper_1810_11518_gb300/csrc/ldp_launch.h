@@ -75,6 +75,24 @@ cudaError_t launch_batch_main(int mode, int k, bool hist, int variant, int grid,
 // Resident CTAs per SM of the persistent kernel.
 cudaError_t batch_occupancy(int mode, int k, bool hist, int variant, int* blocks_per_sm);
 
+// Sliding windows (ldp_windows.cu): wh x ww pixels at stride (sh, sw); bins
+// are C(8,k) compact codes when compact (k >= 1), else the 256 raw codes.
+struct WindowGeom {
+    int wh, ww, sh, sw;
+    int nbins, k, compact;
+};
+// uint32 words of the cell histograms of one H x W image
+uint64_t window_cell_words(int H, int W, const WindowGeom& g);
+// stride = size: the cells are the windows (no cell scratch, no sum pass)
+bool window_direct(const WindowGeom& g);
+// Window histograms of `count` images from their code maps: descriptors in
+// device memory (d_descs) or one by value (one, count = 1); max_H / max_W
+// bound the images' sizes; cells: scratch of cell_stride words per image
+// (unused when window_direct).
+cudaError_t launch_windows(const ldp_image_desc* d_descs, const ldp_image_desc* one, int count, int max_H,
+                           int max_W, const WindowGeom& g, uint32_t* hist, uint32_t* cells,
+                           uint64_t cell_stride, cudaStream_t s);
+
 cudaError_t read_clear_status(cudaStream_t s, int* out);
 // Device address of the status word on the current device (looked up once per device).
 int* status_word();

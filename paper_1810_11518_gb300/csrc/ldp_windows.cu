@@ -1,0 +1,186 @@
+// Sliding-window code histograms (Sec. 3.2): windows of wh x ww pixels at
+// stride (sh, sw) over the image, window (a, b) covering image rows
+// [a*sh, min(a*sh + wh, H)) and columns [b*sw, min(b*sw + ww, W)), interior
+// pixels only.  Every window is a union of cells of the grid with cell size
+// (gcd(wh, sh), gcd(ww, sw)), so the work is
+//   k_cell_hist:   one pass over the code map; a CTA owns a row of cells (a
+//                  chunk of it for wide images) and counts its codes in
+//                  shared memory, then stores the cells' histograms (no
+//                  global atomics: every cell belongs to exactly one CTA);
+//   k_window_sum:  each window histogram is the sum of its cells' (skipped
+//                  when stride = size: the cells are the windows).
+// Images come from ldp_image_desc records (batches) or one record passed by
+// value (single image).
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "ldp_device.cuh"
+#include "ldp_launch.h"
+
+namespace ldp {
+
+namespace {
+
+constexpr int kCellThreads = 256;
+constexpr int kCellSmemWords = 12160;  // counters: with the 512-byte table, 48 KB of static shared memory
+
+struct CellArgs {
+    const ldp_image_desc* descs;  // nullptr: the single image `one`
+    ldp_image_desc one;
+    int ch, cw;        // cell size in pixels
+    int nbins, k;      // k >= 1 with compact bins: C(8,k) bins; else 256 raw bins
+    int chunk;         // cells per CTA along a row
+    int direct;        // 1: cells are the windows, stored at hist + hist_offset
+    uint32_t* hist;    // window histograms (direct) ...
+    uint32_t* cells;   // ... or cell histograms, image i at cells + i * cell_stride
+    uint64_t cell_stride;
+};
+
+__device__ __forceinline__ ldp_image_desc desc_of(const CellArgs& a, int i) {
+    return a.descs ? a.descs[i] : a.one;
+}
+
+// CTA work item p = (image, cell row) pairs, strided over the grid; the
+// grid's y index picks the chunk of cells along the row.
+__global__ void __launch_bounds__(kCellThreads) k_cell_hist(CellArgs a, int count, int ncr_max) {
+    __shared__ uint32_t cnt[kCellSmemWords];
+    __shared__ int16_t lut[256];
+    for (int c = threadIdx.x; c < 256; c += blockDim.x)
+        lut[c] = (a.k >= 1) ? __ldg(&g_bin_table.bin[a.k][c]) : (int16_t)c;
+    const uint64_t pairs = (uint64_t)count * (uint64_t)ncr_max;
+    for (uint64_t p = blockIdx.x; p < pairs; p += gridDim.x) {
+        const int img = (int)(p / (uint64_t)ncr_max), i = (int)(p % (uint64_t)ncr_max);
+        const ldp_image_desc d = desc_of(a, img);
+        const int H = d.H, W = d.W;
+        const int ncr = (H + a.ch - 1) / a.ch, ncc = (W + a.cw - 1) / a.cw;
+        const int j0 = blockIdx.y * a.chunk;
+        if (i >= ncr || j0 >= ncc || d.codes == nullptr) continue;  // uniform over the CTA
+        const int j1 = min(j0 + a.chunk, ncc);
+        const int words = (j1 - j0) * a.nbins;
+        __syncthreads();  // lut ready; the previous item's counters are stored
+        for (int e = threadIdx.x; e < words; e += blockDim.x) cnt[e] = 0;
+        __syncthreads();
+        // interior pixels of cell row i, cells j0..j1-1 (code (x, y) at codes[(x-1)*Pc + y-1])
+        const int x0 = max(i * a.ch, 1), x1 = min((i + 1) * a.ch, H - 1);
+        const int y0 = max(j0 * a.cw, 1), y1 = min(j1 * a.cw, W - 1);
+        for (int y = y0 + threadIdx.x; y < y1; y += blockDim.x) {
+            uint32_t* col = cnt + (y / a.cw - j0) * a.nbins;
+            const uint8_t* cp = d.codes + (size_t)(x0 - 1) * (size_t)d.code_pitch + (y - 1);
+            for (int x = x0; x < x1; ++x, cp += d.code_pitch) {
+                const int b = lut[__ldg(cp)];
+                if (b >= 0) atomicAdd(&col[b], 1u);
+            }
+        }
+        __syncthreads();
+        uint32_t* out = a.direct ? a.hist + d.hist_offset : a.cells + (uint64_t)img * a.cell_stride;
+        out += ((size_t)i * (size_t)ncc + (size_t)j0) * (size_t)a.nbins;
+        for (int e = threadIdx.x; e < words; e += blockDim.x) out[e] = cnt[e];
+    }
+}
+
+struct SumArgs {
+    const ldp_image_desc* descs;
+    ldp_image_desc one;
+    int ch, cw, wh_c, ww_c, sh_c, sw_c;  // window size and stride in cells
+    int wh, ww, sh, sw;                  // in pixels (window counts)
+    int nbins;
+    const uint32_t* cells;
+    uint64_t cell_stride;
+    uint32_t* hist;
+};
+
+__device__ __forceinline__ int win_count(int n, int w, int s) { return n <= w ? 1 : (n - w + s - 1) / s + 1; }
+
+__global__ void __launch_bounds__(256) k_window_sum(SumArgs a, int count) {
+    for (int img = blockIdx.y; img < count; img += gridDim.y) {
+        const ldp_image_desc d = a.descs ? a.descs[img] : a.one;
+        const int H = d.H, W = d.W;
+        const int ncr = (H + a.ch - 1) / a.ch, ncc = (W + a.cw - 1) / a.cw;
+        const int nwr = win_count(H, a.wh, a.sh), nwc = win_count(W, a.ww, a.sw);
+        const uint64_t total = (uint64_t)nwr * (uint64_t)nwc * (uint64_t)a.nbins;
+        const uint32_t* cells = a.cells + (uint64_t)img * a.cell_stride;
+        uint32_t* out = a.hist + d.hist_offset;
+        for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+             e += (uint64_t)gridDim.x * blockDim.x) {
+            const int bin = (int)(e % (uint64_t)a.nbins);
+            const uint64_t w = e / (uint64_t)a.nbins;
+            const int wa = (int)(w / (uint64_t)nwc), wb = (int)(w % (uint64_t)nwc);
+            const int i0 = wa * a.sh_c, i1 = min(i0 + a.wh_c, ncr);
+            const int j0 = wb * a.sw_c, j1 = min(j0 + a.ww_c, ncc);
+            uint32_t s = 0;
+            for (int ci = i0; ci < i1; ++ci)
+                for (int cj = j0; cj < j1; ++cj) s += cells[((size_t)ci * ncc + cj) * a.nbins + bin];
+            out[e] = s;
+        }
+    }
+}
+
+int gcd_int(int a, int b) {
+    while (b) {
+        const int t = a % b;
+        a = b;
+        b = t;
+    }
+    return a;
+}
+
+}  // namespace
+
+uint64_t window_cell_words(int H, int W, const WindowGeom& g) {
+    const int ch = gcd_int(g.wh, g.sh), cw = gcd_int(g.ww, g.sw);
+    return (uint64_t)((H + ch - 1) / ch) * (uint64_t)((W + cw - 1) / cw) * (uint64_t)g.nbins;
+}
+
+bool window_direct(const WindowGeom& g) { return g.wh == g.sh && g.ww == g.sw; }
+
+cudaError_t launch_windows(const ldp_image_desc* d_descs, const ldp_image_desc* one, int count, int max_H,
+                           int max_W, const WindowGeom& g, uint32_t* hist, uint32_t* cells,
+                           uint64_t cell_stride, cudaStream_t s) {
+    const int ch = gcd_int(g.wh, g.sh), cw = gcd_int(g.ww, g.sw);
+    const bool direct = window_direct(g);
+    CellArgs ca{};
+    ca.descs = d_descs;
+    if (one) ca.one = *one;
+    ca.ch = ch;
+    ca.cw = cw;
+    ca.nbins = g.nbins;
+    ca.k = g.compact ? g.k : 0;
+    ca.chunk = kCellSmemWords / g.nbins;
+    ca.direct = direct ? 1 : 0;
+    ca.hist = hist;
+    ca.cells = cells;
+    ca.cell_stride = cell_stride;
+    const int ncr = (max_H + ch - 1) / ch, ncc = (max_W + cw - 1) / cw;
+    const uint64_t pairs = (uint64_t)count * (uint64_t)ncr;
+    dim3 grid((unsigned)(pairs < (1u << 20) ? pairs : (1u << 20)), (ncc + ca.chunk - 1) / ca.chunk);
+    k_cell_hist<<<grid, kCellThreads, 0, s>>>(ca, count, ncr);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || direct) return e;
+    SumArgs sa{};
+    sa.descs = d_descs;
+    if (one) sa.one = *one;
+    sa.ch = ch;
+    sa.cw = cw;
+    sa.wh_c = g.wh / ch;
+    sa.ww_c = g.ww / cw;
+    sa.sh_c = g.sh / ch;
+    sa.sw_c = g.sw / cw;
+    sa.wh = g.wh;
+    sa.ww = g.ww;
+    sa.sh = g.sh;
+    sa.sw = g.sw;
+    sa.nbins = g.nbins;
+    sa.cells = cells;
+    sa.cell_stride = cell_stride;
+    sa.hist = hist;
+    const uint64_t total = (uint64_t)((max_H <= g.wh) ? 1 : (max_H - g.wh + g.sh - 1) / g.sh + 1) *
+                           (uint64_t)((max_W <= g.ww) ? 1 : (max_W - g.ww + g.sw - 1) / g.sw + 1) *
+                           (uint64_t)g.nbins;
+    const uint64_t blocks = (total + 255) / 256;
+    dim3 grid2((unsigned)(blocks < 4096 ? blocks : 4096), (unsigned)(count < 65535 ? count : 65535));
+    k_window_sum<<<grid2, 256, 0, s>>>(sa, count);
+    return cudaGetLastError();
+}
+
+}  // namespace ldp

@@ -23,7 +23,7 @@ def lib():
 def _declared():
     with open(os.path.join(ROOT, "include", "ldp.h")) as f:
         src = f.read()
-    return re.findall(r"LDP_API\s+(?:int|const char \*)\s*(\w+)\(", src)
+    return re.findall(r"LDP_API\s+(?:int|uint64_t|const char \*)\s*(\w+)\(", src)
 
 
 def test_exports_every_declared_symbol(lib):
@@ -101,3 +101,37 @@ def test_layout_alignment():
     d = lay.descs(1 << 20, 1 << 30)
     assert d["hist_offset"].tolist() == [0, 2352, 4704]
     assert d.itemsize == 40
+
+
+def test_window_host_logic_without_gpu(lib):
+    import oracle
+    from paper_1810_11518_gb300 import _abi
+
+    EINVAL = _abi.LDP_EINVAL
+    for n in range(0, 70, 3):
+        for w in range(1, 30, 4):
+            for s in range(1, 33, 5):
+                assert lib.ldp_window_count(n, w, s) == oracle.window_count(n, w, s)
+    assert lib.ldp_window_count(10, 0, 1) == -1 and lib.ldp_window_count(10, 3, 0) == -1
+    ws = _abi.WindowSpec(20, 20, 10, 10, 1)
+    # overlapping windows: code map + cells of gcd(20, 10) = 10 pixels
+    cells = 49 * 64 * 56 * 4
+    assert lib.ldp_window_scratch_bytes(490, 640, 3, ws, 0) == ((488 * 638 + 255) // 256) * 256 + cells
+    assert lib.ldp_window_scratch_bytes(490, 640, 3, ws, 1) == cells
+    # stride = size: the cells are the windows, no cell scratch
+    assert lib.ldp_window_scratch_bytes(490, 640, 3, _abi.WindowSpec(20, 20, 20, 20, 1), 1) == 0
+    assert lib.ldp_window_scratch_bytes(490, 640, 0, _abi.WindowSpec(20, 20, 20, 20, 1), 1) == 0  # bad spec
+    assert lib.ldp_batch_window_scratch_bytes(8, 490, 640, 0, _abi.WindowSpec(20, 20, 10, 10, 0)) == \
+        8 * 49 * 64 * 256 * 4
+    fake = ctypes.c_void_p(0x1000)
+    assert lib.ldp_window_hist(fake, 10, 10, 10, 3, _abi.WindowSpec(0, 4, 4, 4, 1), fake, None, 0, None, 0,
+                               None) == EINVAL
+    assert lib.ldp_window_hist(fake, 10, 10, 10, 3, _abi.WindowSpec(4, 4, 4, 4, 2), fake, None, 0, None, 0,
+                               None) == EINVAL
+    # the code map needs scratch when no code buffer is given
+    assert lib.ldp_window_hist(fake, 10, 10, 10, 3, _abi.WindowSpec(4, 4, 4, 4, 1), fake, None, 0, None, 0,
+                               None) == EINVAL
+    assert lib.lbp_window_hist(fake, 10, 10, 10, _abi.WindowSpec(4, 4, 4, 4, 1), fake, fake, 8, None, 0,
+                               None) == EINVAL
+    assert lib.ldp_batch_window_hist(None, 1, 10, 10, 3, ws, fake, None, 0, None) == EINVAL
+    assert lib.ldp_batch_window_hist(fake, 1, 10, 10, 3, ws, fake, None, 0, None) == EINVAL  # no scratch
