@@ -28,6 +28,9 @@ _lib = None
 
 MODE_LDP = 0
 MODE_LBP = 1
+MODE_LDP_RAW = 2         # rank by the signed response m_i, exactly k bits
+MODE_LDP_THRESH = 3      # rank by |m_i|, every bit tied with the k-th set
+MODE_LDP_RAW_THRESH = 4  # rank by m_i, every bit tied with the k-th set
 
 
 def build(force: bool = False) -> str:
@@ -54,6 +57,7 @@ def _load():
                 fn.restype = None
             lib.oracle_code_from_responses.argtypes = [vp, i32]
             lib.rank_code_from_responses.argtypes = [vp, i32]
+            lib.oracle_code_variant.argtypes = [vp, i32, i32]
             lib.oracle_lbp_code.argtypes = [vp, i32, i32, i32, i32, i32]
             lib.oracle_codes_rect.argtypes = [vp, i32, i32, i32, i32, i32, i32, i32, i32, i32, vp, i32]
             lib.oracle_compact_codes.argtypes = [i32, vp]
@@ -108,6 +112,12 @@ def ringsum_responses(img, x, y):
 def code_from_responses(m, k: int = 3) -> int:
     m = np.ascontiguousarray(m, dtype=np.int32)
     return int(_load().oracle_code_from_responses(m.ctypes.data, k))
+
+
+def code_variant(m, k: int = 3, variant: int = 0) -> int:
+    """Eq. 2-3 readings: 0 |m| exact-k, 1 raw m exact-k, 2 |m| threshold, 3 raw m threshold."""
+    m = np.ascontiguousarray(m, dtype=np.int32)
+    return int(_load().oracle_code_variant(m.ctypes.data, k, variant))
 
 
 def rank_code_from_responses(m, k: int = 3) -> int:
@@ -174,7 +184,7 @@ def band(n: int, nb: int, b: int) -> tuple[int, int]:
 
 
 def nbins(mode: int, k: int, compact: bool) -> int:
-    return len(compact_codes(k)) if (mode == MODE_LDP and compact) else 256
+    return len(compact_codes(k)) if (mode in (MODE_LDP, MODE_LDP_RAW) and compact) else 256
 
 
 def region_hist(code_map, H, W, R, C, nbins_k) -> np.ndarray:
@@ -217,7 +227,7 @@ def extract_windows(img, k: int = 3, window=(20, 20), stride=None, compact: bool
     H, W = img.shape
     stride = tuple(window) if stride is None else tuple(stride)
     cm = codes(img, k=k, mode=mode)
-    nbk = k if (mode == MODE_LDP and compact) else 0
+    nbk = k if (mode in (MODE_LDP, MODE_LDP_RAW) and compact) else 0
     return window_hist(cm, H, W, window[0], window[1], stride[0], stride[1], nbk), cm
 
 

@@ -69,6 +69,38 @@ int oracle_code_from_responses(const int32_t m[8], int k) {
     return code;
 }
 
+/* Eq. 2-3 under each reading of the printed formula.  The ranking value v_i
+ * is |m_i| (variants 0, 2) or the signed response m_i (variants 1, 3).
+ * Variants 0 / 1 set the first k indices of a stable sort by v descending
+ * (exactly k bits, ties to the lower index); variants 2 / 3 apply s(x >= 0)
+ * of Eq. 3 literally against the k-th index of that order, so every
+ * response tied with it is set as well (k or more bits). */
+int oracle_code_variant(const int32_t m[8], int k, int variant) {
+    int32_t v[8];
+    int order[8];
+    for (int i = 0; i < 8; ++i) {
+        v[i] = (variant & 1) ? m[i] : iabs32(m[i]);
+        order[i] = i;
+    }
+    for (int i = 1; i < 8; ++i) {
+        int o = order[i], j = i - 1;
+        while (j >= 0 && v[order[j]] < v[o]) {
+            order[j + 1] = order[j];
+            --j;
+        }
+        order[j + 1] = o;
+    }
+    int code = 0;
+    if (variant < 2) {
+        for (int r = 0; r < k && r < 8; ++r) code |= 1 << order[r];
+    } else {
+        const int32_t t = v[order[k - 1]];
+        for (int i = 0; i < 8; ++i)
+            if (v[i] - t >= 0) code |= 1 << i;
+    }
+    return code;
+}
+
 /* Sec. 2.1: threshold the 8-neighbourhood at the centre value; neighbour j
  * taken counter-clockwise from East, like the mask numbering. */
 int oracle_lbp_code(const uint8_t *img, int H, int W, int pitch, int x, int y) {
@@ -86,7 +118,8 @@ int oracle_codes_rect(const uint8_t *img, int H, int W, int pitch, int mode, int
                       int y0, int y1, uint8_t *codes, int code_pitch) {
     if (!img || !codes || H < 3 || W < 3 || pitch < W) return -1;
     if (x0 < 1 || y0 < 1 || x1 > H - 1 || y1 > W - 1 || x0 > x1 || y0 > y1) return -1;
-    if (mode == 0 && (k < 1 || k > 7)) return -1;
+    if (mode < 0 || mode > 4) return -1;
+    if (mode != 1 && (k < 1 || k > 7)) return -1;
     for (int x = x0; x < x1; ++x)
         for (int y = y0; y < y1; ++y) {
             int code;
@@ -94,6 +127,10 @@ int oracle_codes_rect(const uint8_t *img, int H, int W, int pitch, int mode, int
                 int32_t m[8];
                 oracle_responses(img, H, W, pitch, x, y, m);
                 code = oracle_code_from_responses(m, k);
+            } else if (mode >= 2) {
+                int32_t m[8];
+                oracle_responses(img, H, W, pitch, x, y, m);
+                code = oracle_code_variant(m, k, mode - 1);
             } else {
                 code = oracle_lbp_code(img, H, W, pitch, x, y);
             }
@@ -204,8 +241,8 @@ int oracle_window_hist(const uint8_t *codes, int H, int W, int code_pitch, int w
 int oracle_extract(const uint8_t *img, int H, int W, int pitch, int mode, int k, int R, int C,
                    int compact, uint32_t *hist, uint8_t *codes, int code_pitch) {
     if (!img || H < 3 || W < 3 || pitch < W) return -1;
-    if (mode != 0 && mode != 1) return -1;
-    if (mode == 0 && (k < 1 || k > 7)) return -1;
+    if (mode < 0 || mode > 4) return -1;
+    if (mode != 1 && (k < 1 || k > 7)) return -1;
     int own = 0;
     if (!codes) {
         code_pitch = W - 2;
@@ -215,7 +252,8 @@ int oracle_extract(const uint8_t *img, int H, int W, int pitch, int mode, int k,
     }
     int rc = oracle_codes_rect(img, H, W, pitch, mode, k, 1, H - 1, 1, W - 1, codes, code_pitch);
     if (rc == 0 && hist)
-        rc = oracle_region_hist(codes, H, W, code_pitch, R, C, (mode == 0 && compact) ? k : 0, hist);
+        rc = oracle_region_hist(codes, H, W, code_pitch, R, C, ((mode == 0 || mode == 2) && compact) ? k : 0,
+                                hist);
     if (own) free(codes);
     return rc;
 }

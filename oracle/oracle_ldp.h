@@ -48,12 +48,19 @@ void oracle_responses(const uint8_t *img, int H, int W, int pitch, int x, int y,
 /* Eq. 2-3: stable sort of 0..7 by |m_i| descending, first k indices set. */
 int oracle_code_from_responses(const int32_t m[8], int k);
 
+/* Eq. 2-3 under each reading of the printed formula: ranking value |m_i|
+ * (variant 0, 2) or m_i (1, 3); exactly k bits with ties to the lower index
+ * (0, 1) or every bit with v_i >= v of the k-th ranked index (2, 3).
+ * Variant 0 equals oracle_code_from_responses. */
+int oracle_code_variant(const int32_t m[8], int k, int variant);
+
 /* LBP label at interior pixel (x, y) (Sec. 2.1). */
 int oracle_lbp_code(const uint8_t *img, int H, int W, int pitch, int x, int y);
 
 /* Codes for interior pixels x in [x0,x1), y in [y0,y1) (image coordinates).
  * Code of (x, y) goes to codes[(x - x0) * code_pitch + (y - y0)].
- * mode: 0 = LDP with this k, 1 = LBP (k ignored).  Returns 0 or -1. */
+ * mode: 0 = LDP with this k, 1 = LBP (k ignored), 2 / 3 / 4 = LDP code
+ * variants 1 / 2 / 3 of oracle_code_variant.  Returns 0 or -1. */
 int oracle_codes_rect(const uint8_t *img, int H, int W, int pitch, int mode, int k,
                       int x0, int x1, int y0, int y1, uint8_t *codes, int code_pitch);
 
@@ -88,7 +95,8 @@ int oracle_window_hist(const uint8_t *codes, int H, int W, int code_pitch, int w
                        int sw, int nbins_k, uint32_t *hist);
 
 /* Whole path for one image: codes (optional, may be NULL) + region hists.
- * mode 0 = LDP(k), 1 = LBP; compact selects C(8,k) bins (LDP only). */
+ * mode as oracle_codes_rect; compact selects C(8,k) bins for the exact-k
+ * LDP modes 0 and 2 (the threshold modes always count 256 raw bins). */
 int oracle_extract(const uint8_t *img, int H, int W, int pitch, int mode, int k, int R, int C,
                    int compact, uint32_t *hist, uint8_t *codes, int code_pitch);
 
