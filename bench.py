@@ -224,6 +224,61 @@ def time_batch(ldp, torch, dev, Hs, Ws, seeds, ks, regions, sigma, steps, tune=T
     return out
 
 
+def time_windows(ldp, torch, dev, n, H, W, k, window, stride, steps):
+    """Sliding-window leg (Sec. 3.2): one batch plan run storing the codes of
+    n H x W images, then the window histograms of all of them in one call."""
+    import synth
+    from paper_1810_11518_gb300 import autotune
+
+    lay = ldp.BatchLayout.build([H] * n, [W] * n, hist_len=0)
+    host = torch.empty(lay.img_bytes, dtype=torch.uint8, pin_memory=True)
+    synth.batch_into(host.numpy(), np.arange(n), lay.Hs, lay.Ws, lay.pitches, lay.img_off, sigma=3.0)
+    d_img = host.to(dev)
+    del host
+    d_codes = torch.empty(lay.code_bytes, dtype=torch.uint8, device=dev)
+    sh, sw = window if stride is None else stride
+    nwin = ldp.window_count(H, window[0], sh) * ldp.window_count(W, window[1], sw)
+    per = nwin * ldp.hist_bins(k)
+    descs = lay.descs(d_img.data_ptr(), d_codes.data_ptr())
+    descs["hist_offset"] = np.arange(n, dtype=np.uint64) * np.uint64(per)
+    d_desc = torch.from_numpy(descs.view(np.uint8)).to(dev)
+    d_count = torch.tensor([n], dtype=torch.int32, device=dev)
+    d_hist = torch.empty(n * per, dtype=torch.int32, device=dev)
+    with ldp.BatchPlan(n, lay.pixels, k=k, regions=(1, 1)) as plan:
+        props = torch.cuda.get_device_properties(dev)
+        ent = autotune.lookup(torch.cuda.get_device_name(dev), props.multi_processor_count, "batch", k,
+                              "hist+codes", lay.pixels / n)
+        if ent:
+            plan.set_config(ent["variant"], ent["ctas_per_sm"])
+
+        def step():
+            plan.run(d_desc, d_count, None)
+            ldp.batch_window_hist(d_desc, n, (H, W), k, window, stride, hist=d_hist)
+
+        for _ in range(3):
+            step()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        tw = 0.0
+        torch.cuda.synchronize(dev)
+        ev[0].record()
+        for _ in range(steps):
+            step()
+        ev[1].record()
+        torch.cuda.synchronize(dev)
+        ms = ev[0].elapsed_time(ev[1]) / steps
+        for _ in range(steps):  # the window pass alone, on the same code maps
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            ldp.batch_window_hist(d_desc, n, (H, W), k, window, stride, hist=d_hist)
+            e1.record()
+            torch.cuda.synchronize(dev)
+            tw += e0.elapsed_time(e1)
+    return {"images": n, "height": H, "width": W, "k": k, "window": list(window),
+            "stride": list(window if stride is None else stride), "windows_per_image": nwin,
+            "ms_per_step": round(ms, 4), "value": round(lay.pixels / (ms * 1e-3) / 1e6, 3), "unit": UNIT,
+            "window_pass_ms": round(tw / steps, 4)}
+
+
 def run_reference(a):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -431,6 +486,13 @@ def main():
         sizes = [synth.sizes(s, 64, 1024) for s in range(2048)]
         extras["uneven_batched"] = time_batch(ldp, torch, dev, [h for h, _ in sizes], [w for _, w in sizes],
                                               np.arange(2048), [k], (7, 6), 3.0, max(5, a.steps // 4))[0]
+    if not a.no_extras and rank == 0:
+        # Table 3 windows on the paper's 260 x 260 face crops, and overlapping
+        # windows (stride half the size) on the 640 x 490 batch
+        extras["windows"] = [
+            time_windows(ldp, torch, dev, 4096, 260, 260, k, (20, 20), None, max(5, a.steps // 10)),
+            time_windows(ldp, torch, dev, 4096, 490, 640, k, (20, 20), (10, 10), max(5, a.steps // 10)),
+        ]
     if a.large and rank == 0:
         # ---- large images: 64 x 8192^2 (sigma 6), 16x16 regions, k = 1..4 ----
         extras["large_batched"] = time_batch(ldp, torch, dev, [8192] * 64, [8192] * 64, np.arange(64), (1, 2, 3, 4),

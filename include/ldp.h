@@ -113,6 +113,27 @@ LDP_API int lbp_codes(const uint8_t *d_img, int H, int W, int pitch, uint8_t *d_
 LDP_API int lbp_region_hist(const uint8_t *d_img, int H, int W, int pitch, int R, int C, uint32_t *d_hist,
                     uint8_t *d_codes_or_null, int code_pitch, void *stream);
 
+/* ---- readings of Eq. 2-3 (code modes) ----
+ * Eq. 2 sets s(m_i - m_k) for the k-th "most outstanding" response; the
+ * printed formula leaves the ranking (|m_i| or m_i) and the treatment of ties
+ * open.  LDP_CODE_ABS is the default everywhere else in this API. */
+#define LDP_CODE_ABS 0        /* the k largest |m_i|, exactly k bits, ties to the lower index */
+#define LDP_CODE_RAW 1        /* the k largest signed m_i, exactly k bits, ties to the lower index */
+#define LDP_CODE_ABS_THRESH 2 /* every i with |m_i| >= the k-th largest |m| (k or more bits) */
+#define LDP_CODE_RAW_THRESH 3 /* every i with m_i >= the k-th largest m (k or more bits) */
+
+/* ldp_codes with a code mode (LDP_CODE_*).  EINVAL as ldp_codes, plus
+ * code_mode out of range. */
+LDP_API int ldp_codes_ex(const uint8_t *d_img, int H, int W, int pitch, int k, int code_mode, uint8_t *d_codes,
+                         int code_pitch, void *stream);
+
+/* ldp_region_hist with a code mode.  The threshold modes produce codes of k
+ * or more bits, so they count 256 raw bins: rs.compact must be 0 (EINVAL
+ * otherwise). */
+LDP_API int ldp_region_hist_ex(const uint8_t *d_img, int H, int W, int pitch, int k, int code_mode,
+                               ldp_region_spec rs, uint32_t *d_hist, uint8_t *d_codes_or_null, int code_pitch,
+                               void *stream);
+
 /* ---- sliding windows (Sec. 3.2, Table 3) ---- */
 
 /* Windows of wh x ww pixels whose origins step by (sh, sw): window (a, b)
@@ -174,6 +195,10 @@ typedef struct ldp_batch_plan ldp_batch_plan;
 
 #define LDP_PLAN_LBP 1u       /* plan runs LBP (k ignored, 256 bins) */
 #define LDP_PLAN_NO_GRAPH 2u  /* launch kernels directly instead of replaying a CUDA graph */
+/* code mode of an LDP plan (LDP_CODE_*, default LDP_CODE_ABS); plans of the
+ * other modes run one fixed tile shape (ldp_batch_plan_set_config keeps the
+ * CTAs per SM only) */
+#define LDP_PLAN_CODE_MODE(m) (((unsigned)(m) & 3u) << 2)
 
 /* Creates a plan for batches of up to max_images images holding up to
  * max_pixels pixels in total.  The plan owns its device work-list scratch

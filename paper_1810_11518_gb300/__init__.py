@@ -23,7 +23,7 @@ from ._abi import LdpError, RegionSpec, WindowSpec
 __all__ = ["codes", "region_hist", "lbp_codes", "lbp_region_hist", "hist_bins", "bin_of_code",
            "BatchPlan", "BatchLayout", "DESC_DTYPE", "LdpError", "device_status", "num_variants",
            "variant_name", "set_plain_variant", "load", "batch_run_noalloc", "window_count", "window_hist",
-           "lbp_window_hist", "batch_window_hist"]
+           "lbp_window_hist", "batch_window_hist", "CODE_ABS", "CODE_RAW", "CODE_ABS_THRESH", "CODE_RAW_THRESH"]
 
 DESC_DTYPE = np.dtype([("img", "<u8"), ("H", "<i4"), ("W", "<i4"), ("pitch", "<i4"),
                        ("code_pitch", "<i4"), ("codes", "<u8"), ("hist_offset", "<u8")])
@@ -78,17 +78,30 @@ def bin_of_code(code: int, k: int) -> int:
     return int(_abi.load().ldp_bin_of_code(code, k))
 
 
-def codes(img, k: int = 3, out=None, stream=None):
-    """LDP codes (Eq. 1-3) of the interior: uint8 tensor (H-2, W-2)."""
+CODE_ABS, CODE_RAW, CODE_ABS_THRESH, CODE_RAW_THRESH = (_abi.LDP_CODE_ABS, _abi.LDP_CODE_RAW,
+                                                       _abi.LDP_CODE_ABS_THRESH, _abi.LDP_CODE_RAW_THRESH)
+
+
+def codes(img, k: int = 3, out=None, stream=None, code_mode: int = CODE_ABS):
+    """LDP codes (Eq. 1-3) of the interior: uint8 tensor (H-2, W-2).
+
+    code_mode picks the reading of Eq. 2-3 (CODE_ABS: the k largest |m_i|,
+    the default; CODE_RAW: the k largest m_i; *_THRESH: every response tied
+    with the k-th is set as well)."""
     p, H, W, P = _img(img)
     out, pc = _alloc_codes(img, H, W, out)
-    _abi.call("ldp_codes", p, H, W, P, k, ctypes.c_void_p(out.data_ptr()), pc, _stream(stream))
+    if code_mode == CODE_ABS:
+        _abi.call("ldp_codes", p, H, W, P, k, ctypes.c_void_p(out.data_ptr()), pc, _stream(stream))
+    else:
+        _abi.call("ldp_codes_ex", p, H, W, P, k, int(code_mode), ctypes.c_void_p(out.data_ptr()), pc,
+                  _stream(stream))
     return out
 
 
 def region_hist(img, k: int = 3, regions=(1, 1), compact: bool = True, with_codes: bool = True,
-                hist=None, codes_out=None, stream=None):
-    """Fused LDP codes + R x C region histograms (Eq. 1-6).
+                hist=None, codes_out=None, stream=None, code_mode: int = CODE_ABS):
+    """Fused LDP codes + R x C region histograms (Eq. 1-6); code_mode as in codes()
+    (the threshold modes need compact=False).
 
     Returns (hist int32 tensor (R, C, nbins) holding uint32 counts, codes or None)."""
     torch = _torch()
@@ -103,8 +116,12 @@ def region_hist(img, k: int = 3, regions=(1, 1), compact: bool = True, with_code
     if with_codes:
         out, pc = _alloc_codes(img, H, W, codes_out)
         cptr = ctypes.c_void_p(out.data_ptr())
-    _abi.call("ldp_region_hist", p, H, W, P, k, RegionSpec(R, C, int(compact)),
-              ctypes.c_void_p(hist.data_ptr()), cptr, pc, _stream(stream))
+    if code_mode == CODE_ABS:
+        _abi.call("ldp_region_hist", p, H, W, P, k, RegionSpec(R, C, int(compact)),
+                  ctypes.c_void_p(hist.data_ptr()), cptr, pc, _stream(stream))
+    else:
+        _abi.call("ldp_region_hist_ex", p, H, W, P, k, int(code_mode), RegionSpec(R, C, int(compact)),
+                  ctypes.c_void_p(hist.data_ptr()), cptr, pc, _stream(stream))
     return hist, out
 
 
@@ -293,13 +310,14 @@ class BatchPlan:
     sizes (the library's work list and CUDA graph live inside)."""
 
     def __init__(self, max_images: int, max_pixels: int, k: int = 3, regions=(7, 6), compact: bool = True,
-                 lbp: bool = False, graph: bool = True):
+                 lbp: bool = False, graph: bool = True, code_mode: int = CODE_ABS):
         self.lbp = lbp
         self.k = k
         self.regions = tuple(regions)
         self.compact = bool(compact) and not lbp
         self.nbins = comb(8, k) if self.compact else 256
-        flags = (_abi.LDP_PLAN_LBP if lbp else 0) | (0 if graph else _abi.LDP_PLAN_NO_GRAPH)
+        flags = ((_abi.LDP_PLAN_LBP if lbp else 0) | (0 if graph else _abi.LDP_PLAN_NO_GRAPH) |
+                 _abi.plan_code_mode(code_mode))
         h = ctypes.c_void_p()
         _abi.call("ldp_batch_plan_create", ctypes.byref(h), int(max_images), int(max_pixels), int(k),
                   RegionSpec(self.regions[0], self.regions[1], int(self.compact)), flags)

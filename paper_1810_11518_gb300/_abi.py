@@ -18,6 +18,15 @@ STATUS_NAMES = {0: "LDP_OK", 1: "LDP_EINVAL", 2: "LDP_ECUDA", 3: "LDP_ENOMEM", 4
                 5: "LDP_ENOTIMPL"}
 LDP_PLAN_LBP = 1
 LDP_PLAN_NO_GRAPH = 2
+# readings of Eq. 2-3 (code modes)
+LDP_CODE_ABS = 0         # the k largest |m_i|, ties to the lower index
+LDP_CODE_RAW = 1         # the k largest signed m_i, ties to the lower index
+LDP_CODE_ABS_THRESH = 2  # every i with |m_i| >= the k-th largest |m|
+LDP_CODE_RAW_THRESH = 3  # every i with m_i >= the k-th largest m
+
+
+def plan_code_mode(m: int) -> int:
+    return (int(m) & 3) << 2
 
 # Every function include/ldp.h declares (checked by the CPU test suite).
 EXPORTS = [
@@ -28,7 +37,7 @@ EXPORTS = [
     "ldp_batch_plan_enable_timing", "ldp_batch_plan_kernel_times", "ldp_batch_run_noalloc",
     "ldp_server_create", "ldp_server_submit", "ldp_server_poll", "ldp_server_stats", "ldp_server_destroy",
     "ldp_window_count", "ldp_window_scratch_bytes", "ldp_window_hist", "lbp_window_hist",
-    "ldp_batch_window_scratch_bytes", "ldp_batch_window_hist",
+    "ldp_batch_window_scratch_bytes", "ldp_batch_window_hist", "ldp_codes_ex", "ldp_region_hist_ex",
 ]
 
 
@@ -114,6 +123,8 @@ def load(path: str | None = None):
             "ldp_server_stats": [vp, ctypes.POINTER(ServerStats)],
             "ldp_server_destroy": [vp],
             "ldp_window_count": [i32, i32, i32],
+            "ldp_codes_ex": [vp, i32, i32, i32, i32, i32, vp, i32, vp],
+            "ldp_region_hist_ex": [vp, i32, i32, i32, i32, i32, RegionSpec, vp, vp, i32, vp],
             "ldp_window_scratch_bytes": [i32, i32, i32, WindowSpec, i32],
             "ldp_window_hist": [vp, i32, i32, i32, i32, WindowSpec, vp, vp, i32, vp, u64, vp],
             "lbp_window_hist": [vp, i32, i32, i32, WindowSpec, vp, vp, i32, vp, u64, vp],

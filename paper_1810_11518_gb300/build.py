@@ -68,6 +68,13 @@ def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -
         units.append((os.path.join(CSRC, "ldp_kernels.cu"), os.path.join(BUILD, f"ldp_kernels_v{vid}.o"),
                       [f"-DLDP_VAR_ID={vid}", f"-DLDP_VAR_RPW={rpw}", f"-DLDP_VAR_NW={nw}", f"-DLDP_VAR_MB={mb}",
                        f"-DLDP_VAR_ST={st}"]))
+    # the kernels of the other Eq. 2-3 readings (kernel modes 2..4, one unit
+    # each), in the tile shape of variant 0
+    v0 = variants()[0]
+    for cm in (2, 3, 4):
+        units.append((os.path.join(CSRC, "ldp_kernels.cu"), os.path.join(BUILD, f"ldp_kernels_vcm{cm}.o"),
+                      [f"-DLDP_VAR_ID=cm{cm}", f"-DLDP_VAR_RPW={v0[1]}", f"-DLDP_VAR_NW={v0[2]}",
+                       f"-DLDP_VAR_MB={v0[3]}", f"-DLDP_VAR_ST={v0[4]}", f"-DLDP_CODE_MODES={cm}"]))
     cmds = [[cc] + ARCH + FLAGS + inc + defs + ["-c", src, "-o", obj] for src, obj, defs in units]
     jobs = jobs or max(1, min(len(cmds), os.cpu_count() or 1))
     with cf.ThreadPoolExecutor(jobs) as ex:

@@ -59,8 +59,9 @@ int run_plain(int mode, const uint8_t* img, int H, int W, int pitch, int k, int 
     ldp::JobArgs jb{img, H, W, pitch, codes, code_pitch, hist, ldp::status_word()};
     ldp::HistArgs hc{R, C, 256, 0};
     if (hist) {
-        hc.nbins = (mode == 0 && compact) ? binom8(k) : 256;
-        hc.compact = (mode == 0 && compact) ? 1 : 0;
+        const bool exact = mode == ldp::kLDP || mode == ldp::kLDPRaw;  // codes of exactly k bits
+        hc.nbins = (exact && compact) ? binom8(k) : 256;
+        hc.compact = (exact && compact) ? 1 : 0;
         const size_t bytes = (size_t)R * (size_t)C * (size_t)hc.nbins * sizeof(uint32_t);
         cudaError_t e = cudaMemsetAsync(hist, 0, bytes, s);
         if (e != cudaSuccess) return cuda_fail(e, "zeroing the histogram");
@@ -170,6 +171,47 @@ int lbp_region_hist(const uint8_t* d_img, int H, int W, int pitch, int R, int C,
     if ((rc = check_regions(R, C))) return rc;
     if (!d_hist) return fail(LDP_EINVAL, "histogram pointer is NULL");
     return run_plain(1, d_img, H, W, pitch, 1, R, C, 0, d_hist, d_codes_or_null, code_pitch, stream);
+}
+
+namespace {
+// LDP_CODE_* -> kernel mode
+int code_mode_kernel(int code_mode) {
+    switch (code_mode) {
+        case LDP_CODE_ABS: return ldp::kLDP;
+        case LDP_CODE_RAW: return ldp::kLDPRaw;
+        case LDP_CODE_ABS_THRESH: return ldp::kLDPThresh;
+        case LDP_CODE_RAW_THRESH: return ldp::kLDPRawThresh;
+        default: return -1;
+    }
+}
+}  // namespace
+
+int ldp_codes_ex(const uint8_t* d_img, int H, int W, int pitch, int k, int code_mode, uint8_t* d_codes,
+                 int code_pitch, void* stream) {
+    int rc;
+    if ((rc = check_image(d_img, H, W, pitch))) return rc;
+    if ((rc = check_codes(d_codes, W, code_pitch, true))) return rc;
+    if (k < 1 || k > 7) return fail(LDP_EINVAL, "k must be in [1,7]");
+    const int mode = code_mode_kernel(code_mode);
+    if (mode < 0) return fail(LDP_EINVAL, "code_mode must be one of LDP_CODE_*");
+    return run_plain(mode, d_img, H, W, pitch, k, 1, 1, 0, nullptr, d_codes, code_pitch, stream);
+}
+
+int ldp_region_hist_ex(const uint8_t* d_img, int H, int W, int pitch, int k, int code_mode, ldp_region_spec rs,
+                       uint32_t* d_hist, uint8_t* d_codes_or_null, int code_pitch, void* stream) {
+    int rc;
+    if ((rc = check_image(d_img, H, W, pitch))) return rc;
+    if ((rc = check_codes(d_codes_or_null, W, code_pitch, false))) return rc;
+    if (k < 1 || k > 7) return fail(LDP_EINVAL, "k must be in [1,7]");
+    const int mode = code_mode_kernel(code_mode);
+    if (mode < 0) return fail(LDP_EINVAL, "code_mode must be one of LDP_CODE_*");
+    if ((rc = check_regions(rs.R, rs.C))) return rc;
+    if (rs.compact != 0 && rs.compact != 1) return fail(LDP_EINVAL, "compact must be 0 or 1");
+    if (rs.compact && (mode == ldp::kLDPThresh || mode == ldp::kLDPRawThresh))
+        return fail(LDP_EINVAL, "threshold code modes count 256 raw bins (compact = 0)");
+    if (!d_hist) return fail(LDP_EINVAL, "histogram pointer is NULL");
+    return run_plain(mode, d_img, H, W, pitch, k, rs.R, rs.C, rs.compact, d_hist, d_codes_or_null, code_pitch,
+                     stream);
 }
 
 int ldp_window_count(int n, int w, int s) {
@@ -290,11 +332,15 @@ int ldp_batch_plan_create(ldp_batch_plan** out, int max_images, uint64_t max_pix
     *out = nullptr;
     if (max_images < 1 || max_images > (1 << 24)) return fail(LDP_EINVAL, "max_images must be in [1, 1<<24]");
     if (max_pixels < 9) return fail(LDP_EINVAL, "max_pixels must be at least 9");
-    const int mode = (flags & LDP_PLAN_LBP) ? 1 : 0;
-    if (mode == 0 && (k < 1 || k > 7)) return fail(LDP_EINVAL, "k must be in [1,7]");
+    const int cmode = (int)((flags >> 2) & 3u);
+    if ((flags & LDP_PLAN_LBP) && cmode) return fail(LDP_EINVAL, "code modes apply to LDP plans only");
+    const int mode = (flags & LDP_PLAN_LBP) ? 1 : code_mode_kernel(cmode);
+    if (mode != 1 && (k < 1 || k > 7)) return fail(LDP_EINVAL, "k must be in [1,7]");
     int rc;
     if ((rc = check_regions(rs.R, rs.C))) return rc;
     if (rs.compact != 0 && rs.compact != 1) return fail(LDP_EINVAL, "compact must be 0 or 1");
+    if (rs.compact && (mode == ldp::kLDPThresh || mode == ldp::kLDPRawThresh))
+        return fail(LDP_EINVAL, "threshold code modes count 256 raw bins (compact = 0)");
     // Tiles of an image: ceil((H-2)/TH)*ceil((W-2)/128) <= HW/(TH*128) + (H+W)/min(TH,128) + 1,
     // and H + W <= 2HW/3 for H, W >= 3; every variant has TH >= 64.
     const double bound = (double)max_pixels / (64.0 * 128.0) + (2.0 / 3.0) * (double)max_pixels / 64.0 +
@@ -303,7 +349,7 @@ int ldp_batch_plan_create(ldp_batch_plan** out, int max_images, uint64_t max_pix
     ldp_batch_plan* p = new (std::nothrow) ldp_batch_plan();
     if (!p) return fail(LDP_ENOMEM, "host allocation failed");
     p->mode = mode;
-    p->k = mode == 0 ? k : 1;
+    p->k = mode != 1 ? k : 1;
     p->rs = rs;
     if (mode == 1) p->rs.compact = 0;
     p->flags = flags;
@@ -344,7 +390,11 @@ int ldp_batch_plan_set_config(ldp_batch_plan* plan, int variant, int ctas_per_sm
 static int batch_run(ldp_batch_plan* plan, int mode, const ldp_image_desc* d_descs, const int* d_count,
                      uint32_t* d_hist, void* stream) {
     if (!plan) return fail(LDP_EINVAL, "plan is NULL");
-    if (plan->mode != mode) return fail(LDP_EINVAL, "plan was created for the other descriptor (LDP vs LBP)");
+    if ((plan->mode == 1) != (mode == 1))
+        return fail(LDP_EINVAL, "plan was created for the other descriptor (LDP vs LBP)");
+    mode = plan->mode;  // LDP plans carry their code mode
+    // the code-mode kernels have one tile shape (the one of kCodeModeVariant)
+    const int variant = mode >= 2 ? ldp::kCodeModeVariant : plan->variant;
     if (!d_descs || !d_count) return fail(LDP_EINVAL, "descriptor or count pointer is NULL");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     ldp::BatchArgs a{};
@@ -356,12 +406,12 @@ static int batch_run(ldp_batch_plan* plan, int mode, const ldp_image_desc* d_des
     a.scr = plan->scr;
     a.hc.R = plan->rs.R;
     a.hc.C = plan->rs.C;
-    a.hc.compact = (mode == 0 && plan->rs.compact) ? 1 : 0;
+    a.hc.compact = ((mode == ldp::kLDP || mode == ldp::kLDPRaw) && plan->rs.compact) ? 1 : 0;
     a.hc.nbins = a.hc.compact ? binom8(plan->k) : 256;
     a.status = ldp::status_word();
     if (!a.status) return fail(LDP_ECUDA, "device status word not found");
     int occ = 0;
-    cudaError_t e = ldp::batch_occupancy(mode, plan->k, d_hist != nullptr, plan->variant, &occ);
+    cudaError_t e = ldp::batch_occupancy(mode, plan->k, d_hist != nullptr, variant, &occ);
     if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
     if (occ < 1) return fail(LDP_ENOTIMPL, "persistent kernel does not fit on an SM");
     const int per_sm = plan->ctas_per_sm > 0 ? (plan->ctas_per_sm < occ ? plan->ctas_per_sm : occ) : occ;
@@ -374,10 +424,10 @@ static int batch_run(ldp_batch_plan* plan, int mode, const ldp_image_desc* d_des
         if (e != cudaSuccess) return cuda_fail(e, "creating timing events");
     }
     if (plan->flags & LDP_PLAN_NO_GRAPH) {
-        e = ldp::launch_batch_prep(plan->variant, a, s);
+        e = ldp::launch_batch_prep(variant, a, s);
         if (e != cudaSuccess) return cuda_fail(e, "batch preparation launch");
         if (timed) cudaEventRecord(plan->ev_start[plan->nrec], s);
-        e = ldp::launch_batch_main(mode, plan->k, hist, plan->variant, grid, a, s);
+        e = ldp::launch_batch_main(mode, plan->k, hist, variant, grid, a, s);
         if (e != cudaSuccess) return cuda_fail(e, "persistent kernel launch");
         if (timed) {
             e = cudaEventRecord(plan->ev_end[plan->nrec], s);
@@ -387,7 +437,7 @@ static int batch_run(ldp_batch_plan* plan, int mode, const ldp_image_desc* d_des
         return LDP_OK;
     }
     if (!plan->exec || plan->g_descs != d_descs || plan->g_count != d_count || plan->g_hist != d_hist ||
-        plan->g_variant != plan->variant || plan->g_grid != grid) {
+        plan->g_variant != variant || plan->g_grid != grid) {
         if (plan->exec) {
             cudaGraphExecDestroy(plan->exec);
             plan->exec = nullptr;
@@ -403,11 +453,11 @@ static int batch_run(ldp_batch_plan* plan, int mode, const ldp_image_desc* d_des
         cudaGraph_t g = nullptr;
         e = cudaStreamBeginCapture(plan->cap_stream, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return cuda_fail(e, "beginning graph capture");
-        cudaError_t e1 = ldp::launch_batch_prep(plan->variant, a, plan->cap_stream);
+        cudaError_t e1 = ldp::launch_batch_prep(variant, a, plan->cap_stream);
         // external event records become event-record nodes of the captured graph
         if (e1 == cudaSuccess) e1 = cudaEventRecordWithFlags(plan->ph_start, plan->cap_stream, cudaEventRecordExternal);
         cudaError_t e2 = e1 == cudaSuccess
-                             ? ldp::launch_batch_main(mode, plan->k, hist, plan->variant, grid, a, plan->cap_stream)
+                             ? ldp::launch_batch_main(mode, plan->k, hist, variant, grid, a, plan->cap_stream)
                              : e1;
         if (e2 == cudaSuccess) e2 = cudaEventRecordWithFlags(plan->ph_end, plan->cap_stream, cudaEventRecordExternal);
         e = cudaStreamEndCapture(plan->cap_stream, &g);
@@ -441,7 +491,7 @@ static int batch_run(ldp_batch_plan* plan, int mode, const ldp_image_desc* d_des
         plan->g_descs = d_descs;
         plan->g_count = d_count;
         plan->g_hist = d_hist;
-        plan->g_variant = plan->variant;
+        plan->g_variant = variant;
         plan->g_grid = grid;
     }
     cudaEvent_t es = timed ? plan->ev_start[plan->nrec] : plan->ph_start;

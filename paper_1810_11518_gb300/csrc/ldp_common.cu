@@ -133,6 +133,9 @@ cudaError_t launch_batch_prep(int variant, const BatchArgs& a, cudaStream_t s) {
 
 cudaError_t launch_plain(int mode, int k, bool hist, int variant, const JobArgs& jb, const HistArgs& hc,
                          cudaStream_t s) {
+    if (mode == kLDPRaw) return varcm2::launch_plain(mode, k, hist, jb, hc, s);
+    if (mode == kLDPThresh) return varcm3::launch_plain(mode, k, hist, jb, hc, s);
+    if (mode == kLDPRawThresh) return varcm4::launch_plain(mode, k, hist, jb, hc, s);
     switch (variant) {
 #define LDP_CASE(ID, RPW, NW, MB, ST) \
     case ID: return var##ID::launch_plain(mode, k, hist, jb, hc, s);
@@ -144,6 +147,9 @@ cudaError_t launch_plain(int mode, int k, bool hist, int variant, const JobArgs&
 
 cudaError_t launch_batch_main(int mode, int k, bool hist, int variant, int grid, const BatchArgs& a,
                               cudaStream_t s) {
+    if (mode == kLDPRaw) return varcm2::launch_batch_main(mode, k, hist, grid, a, s);
+    if (mode == kLDPThresh) return varcm3::launch_batch_main(mode, k, hist, grid, a, s);
+    if (mode == kLDPRawThresh) return varcm4::launch_batch_main(mode, k, hist, grid, a, s);
     switch (variant) {
 #define LDP_CASE(ID, RPW, NW, MB, ST) \
     case ID: return var##ID::launch_batch_main(mode, k, hist, grid, a, s);
@@ -154,6 +160,9 @@ cudaError_t launch_batch_main(int mode, int k, bool hist, int variant, int grid,
 }
 
 cudaError_t batch_occupancy(int mode, int k, bool hist, int variant, int* blocks_per_sm) {
+    if (mode == kLDPRaw) return varcm2::batch_occupancy(mode, k, hist, blocks_per_sm);
+    if (mode == kLDPThresh) return varcm3::batch_occupancy(mode, k, hist, blocks_per_sm);
+    if (mode == kLDPRawThresh) return varcm4::batch_occupancy(mode, k, hist, blocks_per_sm);
     switch (variant) {
 #define LDP_CASE(ID, RPW, NW, MB, ST) \
     case ID: return var##ID::batch_occupancy(mode, k, hist, blocks_per_sm);

@@ -24,12 +24,14 @@
 #include <cstdint>
 #include <type_traits>
 
+#include "ldp_modes.h"
+
 namespace ldp {
 
 constexpr int kTileW = 128;           // output columns per tile: 32 lanes x 4 columns
 constexpr int kMaxSlots = 16;         // regions a tile may touch and still count in smem
 
-enum Mode { kLDP = 0, kLBP = 1 };
+
 
 // One image of work, as the kernels see it.
 struct Job {
@@ -131,6 +133,37 @@ __device__ __forceinline__ Raw load_raw(const uint8_t* __restrict__ row, int v, 
     return r;
 }
 
+// Threshold reading of Eq. 2-3 for a pair of lanes: t = the K-th smallest
+// key (Batcher's odd-even merge sort of eight, pruned to what s[K-1] needs);
+// every direction whose key is at most t | 7 -- the same ranking value as
+// the K-th or a better one, whatever its index -- is set.  Bytes 0 and 2.
+template <int K>
+__device__ __forceinline__ uint32_t code_thresh(const uint32_t (&key)[8]) {
+    uint32_t s[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) s[i] = key[i];
+    auto cs = [](uint32_t& a, uint32_t& b) {
+        const uint32_t lo = vmin2(a, b), hi = vmax2(a, b);
+        a = lo;
+        b = hi;
+    };
+    cs(s[0], s[1]); cs(s[2], s[3]); cs(s[4], s[5]); cs(s[6], s[7]);
+    cs(s[0], s[2]); cs(s[1], s[3]); cs(s[4], s[6]); cs(s[5], s[7]);
+    cs(s[1], s[2]); cs(s[5], s[6]);
+    cs(s[0], s[4]); cs(s[1], s[5]); cs(s[2], s[6]); cs(s[3], s[7]);
+    cs(s[2], s[4]); cs(s[3], s[5]);
+    cs(s[1], s[2]); cs(s[3], s[4]); cs(s[5], s[6]);
+    const uint32_t t = s[K - 1] | 0x00070007u;
+    const uint32_t t0 = t & 0xFFFFu, t1 = t >> 16;
+    uint32_t c0 = 0, c1 = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        c0 |= (uint32_t)((key[i] & 0xFFFFu) <= t0) << i;
+        c1 |= (uint32_t)((key[i] >> 16) <= t1) << i;
+    }
+    return c0 | (c1 << 16);
+}
+
 // One image row restricted to the six columns v..v+5 a thread needs, in
 // pairs of 16-bit lanes: P[j] = (byte v+j, byte v+j+2), j = 0..3, and the row
 // three-sums T[c] = P[c] + P[c+1] + P[c+2], centred on columns v+1+c, v+3+c.
@@ -188,8 +221,9 @@ __device__ __forceinline__ uint32_t lbp_row4(const BRow& A, const BRow& B, const
 // Codes of the two pixels of lane pair c (c = 0: columns v+1, v+3; c = 1:
 // columns v+2, v+4) of one output row, from rows A (x-1), B (x), C (x+1) and
 // the column three-sums V; bytes 0 and 2 of the result.
-template <int K, int c>
+template <int K, int MODE, int c>
 __device__ __forceinline__ uint32_t ldp_pair(const SRow& A, const SRow& B, const SRow& C, const uint32_t (&V)[4]) {
+    constexpr bool kRaw = MODE == kLDPRaw || MODE == kLDPRawThresh;
     constexpr int L = c, M = c + 1, R = c + 2;  // west, centre and east columns of the pair
     const uint32_t S3[8] = {
         V[R],                       // E : p7 + p0 + p1
@@ -207,22 +241,30 @@ __device__ __forceinline__ uint32_t ldp_pair(const SRow& A, const SRow& B, const
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         // a = 8C - 8 m_i, b = 8C + 8 m_i: one multiply-add each (FMA pipe),
-        // the min and the tie index i on the ALU
+        // the min and the tie index i on the ALU.  Ranking the signed m_i
+        // (kRaw) the key is a + i = 8 (C - m_i) + i, in [0, 61207].
         uint32_t a, b;
         asm("mad.lo.u32 %0, %1, -64, %2;" : "=r"(a) : "r"(S3[i]), "r"(Za));
-        asm("mad.lo.u32 %0, %1, 64, %2;" : "=r"(b) : "r"(S3[i]), "r"(Zb));
-        key[i] = vmin2(a, b) + (uint32_t)i * 0x00010001u;
+        if constexpr (kRaw) {
+            key[i] = a + (uint32_t)i * 0x00010001u;
+        } else {
+            asm("mad.lo.u32 %0, %1, 64, %2;" : "=r"(b) : "r"(S3[i]), "r"(Zb));
+            key[i] = vmin2(a, b) + (uint32_t)i * 0x00010001u;
+        }
     }
-    return code_pair<K>(key);
+    if constexpr (exact_k(MODE))
+        return code_pair<K>(key);
+    else
+        return code_thresh<K>(key);
 }
 
 // Codes of the four pixels of one output row (byte t = column v+t).
-template <int K>
+template <int K, int MODE>
 __device__ __forceinline__ uint32_t ldp_row4(const SRow& A, const SRow& B, const SRow& C) {
     uint32_t V[4];  // column three-sums
 #pragma unroll
     for (int j = 0; j < 4; ++j) V[j] = A.P[j] + B.P[j] + C.P[j];
-    const uint32_t c02 = ldp_pair<K, 0>(A, B, C, V), c13 = ldp_pair<K, 1>(A, B, C, V);
+    const uint32_t c02 = ldp_pair<K, MODE, 0>(A, B, C, V), c13 = ldp_pair<K, MODE, 1>(A, B, C, V);
     return __byte_perm(c02, c13, 0x6240u);
 }
 
@@ -407,7 +449,7 @@ __device__ __forceinline__ void warp_tile(const Job& jb, const HistCfg& hc, int 
     int ri = ri_lo, next_b = 0, rowb = 0;
     // shared-memory byte address of bin 0 of each column's current slot
     uint32_t sbase[4] = {0u, 0u, 0u, 0u};
-    const uint32_t wh_addr = HIST && use_smem && MODE == kLDP ? smem_addr(wh) : 0u;
+    const uint32_t wh_addr = HIST && use_smem && is_ldp(MODE) ? smem_addr(wh) : 0u;
     auto set_sbase = [&]() {
 #pragma unroll
         for (int t = 0; t < 4; ++t) sbase[t] = wh_addr + 4u * (uint32_t)(rowb + colb[t]);
@@ -415,7 +457,7 @@ __device__ __forceinline__ void warp_tile(const Job& jb, const HistCfg& hc, int 
     if constexpr (HIST) {
         next_b = band_lo(ri + 1, H, hc.R);
         rowb = use_smem ? 0 : ri * hc.C;
-        if (use_smem && MODE == kLDP) set_sbase();
+        if (use_smem && is_ldp(MODE)) set_sbase();
     }
 
     // codes of output row u (byte t of `packed` = column v+t) -> code map and histogram
@@ -435,9 +477,9 @@ __device__ __forceinline__ void warp_tile(const Job& jb, const HistCfg& hc, int 
                 ++ri;
                 next_b = band_lo(ri + 1, H, hc.R);
                 rowb = use_smem ? (ri - ri_lo) * ncs * 256 : ri * hc.C;
-                if (use_smem && MODE == kLDP) set_sbase();
+                if (use_smem && is_ldp(MODE)) set_sbase();
             }
-            if (use_smem && MODE == kLDP) {
+            if (use_smem && is_ldp(MODE)) {
                 // LDP codes spread over the bins: one byte extract, one
                 // multiply-add for the address, one reduction per pixel
 #pragma unroll
@@ -465,14 +507,14 @@ __device__ __forceinline__ void warp_tile(const Job& jb, const HistCfg& hc, int 
         }
     };
     auto codes_of_row = [&](const auto& A, const auto& B, const auto& C) -> uint32_t {
-        if constexpr (MODE == kLDP)
-            return ldp_row4<K>(A, B, C);
+        if constexpr (is_ldp(MODE))
+            return ldp_row4<K, MODE>(A, B, C);
         else
             return lbp_row4(A, B, C);
     };
-    using Row = std::conditional_t<MODE == kLDP, SRow, BRow>;
+    using Row = std::conditional_t<is_ldp(MODE), SRow, BRow>;
     auto unpack = [&](const Raw& w, Row& r) {
-        if constexpr (MODE == kLDP)
+        if constexpr (is_ldp(MODE))
             unpack_srow(w, r);
         else
             unpack_brow(w, r);
@@ -592,15 +634,16 @@ __device__ __forceinline__ void warp_tile(const Job& jb, const HistCfg& hc, int 
         if (use_smem) {
             __syncwarp();
             // Only codes that can occur are scanned: the C(8,k) codes with
-            // popcount k for LDP (bin = position in the list when compact,
-            // the code itself when raw), all 256 for LBP.
-            constexpr int NC = (MODE == kLDP) ? binom_ce(8, K) : 256;
+            // popcount k for the exact-k LDP modes (bin = position in the
+            // list when compact, the code itself when raw), all 256 for LBP
+            // and the threshold modes.
+            constexpr int NC = exact_k(MODE) ? binom_ce(8, K) : 256;
             constexpr int NI = (NC + 31) / 32;
             int code_of[NI];
 #pragma unroll
             for (int m = 0; m < NI; ++m) {
                 const int idx = lane + 32 * m;
-                code_of[m] = (MODE == kLDP) ? (idx < NC ? (int)__ldg(&g_code_list.code[K][idx]) : -1) : idx;
+                code_of[m] = exact_k(MODE) ? (idx < NC ? (int)__ldg(&g_code_list.code[K][idx]) : -1) : idx;
             }
             for (int sl = 0; sl < nslots; ++sl) {
                 const int hbase = ((ri_lo + sl / ncs) * hc.C + rj_lo + sl % ncs) * hc.nbins;
@@ -611,7 +654,7 @@ __device__ __forceinline__ void warp_tile(const Job& jb, const HistCfg& hc, int 
                     if (code >= 0) {
                         const uint32_t c = hs[code];
                         if (c) {
-                            const int bin = (MODE == kLDP && hc.compact) ? lane + 32 * m : code;
+                            const int bin = (exact_k(MODE) && hc.compact) ? lane + 32 * m : code;
                             atomicAdd(&jb.hist[hbase + bin], c);
                             hs[code] = 0;
                         }

@@ -2,7 +2,10 @@
 // once per variant with -DLDP_VAR_ID=<n> -DLDP_VAR_RPW=<rows> -DLDP_VAR_NW=<warps>
 // -DLDP_VAR_MB=<min CTAs per SM> -DLDP_VAR_ST=<1: rows staged through the bulk-copy engine>:
 // the single-image fused kernel and the persistent batch kernel for every
-// (mode, k, histogram) combination, plus their launchers.
+// (mode, k, histogram) combination, plus their launchers.  Built once more
+// per other reading of Eq. 2-3 with -DLDP_CODE_MODES=<kernel mode> (raw-m
+// ranking, thresholds; namespaces varcm2..varcm4), in the tile shape of
+// variant 0.
 #include <cuda_runtime.h>
 
 #include "ldp_device.cuh"
@@ -131,6 +134,16 @@ __global__ void __launch_bounds__(V::NW * 32, V::MB) k_batch(BatchArgs a) {
 }
 
 // ---------------- dispatch ----------------
+#define LDP_KCASES(X, M)     \
+    case 1: X(M, 1); break; \
+    case 2: X(M, 2); break; \
+    case 3: X(M, 3); break; \
+    case 4: X(M, 4); break; \
+    case 5: X(M, 5); break; \
+    case 6: X(M, 6); break; \
+    case 7: X(M, 7); break; \
+    default: return cudaErrorInvalidValue;
+
 cudaError_t launch_plain(int mode, int k, bool hist, const JobArgs& jb, const HistArgs& hc, cudaStream_t s) {
     const int tiles = ((jb.W - 2 + kTileW - 1) / kTileW) * ((jb.H - 2 + VAR::RPW - 1) / VAR::RPW);
     dim3 grid((tiles + VAR::NW - 1) / VAR::NW);
@@ -140,38 +153,45 @@ cudaError_t launch_plain(int mode, int k, bool hist, const JobArgs& jb, const Hi
         if (hist) k_plain<M, KK, VAR, true><<<grid, block, 0, s>>>(jb, hc);     \
         else k_plain<M, KK, VAR, false><<<grid, block, 0, s>>>(jb, hc);         \
     } while (0)
-    if (mode == kLBP) {
-        LDP_PLAIN(kLBP, 1);
-    } else {
-        switch (k) {
-            case 1: LDP_PLAIN(kLDP, 1); break;
-            case 2: LDP_PLAIN(kLDP, 2); break;
-            case 3: LDP_PLAIN(kLDP, 3); break;
-            case 4: LDP_PLAIN(kLDP, 4); break;
-            case 5: LDP_PLAIN(kLDP, 5); break;
-            case 6: LDP_PLAIN(kLDP, 6); break;
-            case 7: LDP_PLAIN(kLDP, 7); break;
-            default: return cudaErrorInvalidValue;
-        }
+    switch (mode) {
+#ifdef LDP_CODE_MODES
+        case LDP_CODE_MODES: switch (k) { LDP_KCASES(LDP_PLAIN, LDP_CODE_MODES) } break;
+#else
+        case kLBP: LDP_PLAIN(kLBP, 1); break;
+        case kLDP: switch (k) { LDP_KCASES(LDP_PLAIN, kLDP) } break;
+#endif
+        default: return cudaErrorInvalidValue;
     }
 #undef LDP_PLAIN
     return cudaGetLastError();
 }
 
-static const void* batch_fn(int mode, int k, bool hist) {
-#define LDP_BFN(M, KK) (hist ? (const void*)k_batch<M, KK, VAR, true> : (const void*)k_batch<M, KK, VAR, false>)
-    if (mode == kLBP) return LDP_BFN(kLBP, 1);
+template <int M>
+static const void* batch_fn_k(int k, bool hist) {
+#define LDP_BFN(KK) (hist ? (const void*)k_batch<M, KK, VAR, true> : (const void*)k_batch<M, KK, VAR, false>)
     switch (k) {
-        case 1: return LDP_BFN(kLDP, 1);
-        case 2: return LDP_BFN(kLDP, 2);
-        case 3: return LDP_BFN(kLDP, 3);
-        case 4: return LDP_BFN(kLDP, 4);
-        case 5: return LDP_BFN(kLDP, 5);
-        case 6: return LDP_BFN(kLDP, 6);
-        case 7: return LDP_BFN(kLDP, 7);
+        case 1: return LDP_BFN(1);
+        case 2: return LDP_BFN(2);
+        case 3: return LDP_BFN(3);
+        case 4: return LDP_BFN(4);
+        case 5: return LDP_BFN(5);
+        case 6: return LDP_BFN(6);
+        case 7: return LDP_BFN(7);
         default: return nullptr;
     }
 #undef LDP_BFN
+}
+
+static const void* batch_fn(int mode, int k, bool hist) {
+    switch (mode) {
+#ifdef LDP_CODE_MODES
+        case LDP_CODE_MODES: return batch_fn_k<LDP_CODE_MODES>(k, hist);
+#else
+        case kLBP: return hist ? (const void*)k_batch<kLBP, 1, VAR, true> : (const void*)k_batch<kLBP, 1, VAR, false>;
+        case kLDP: return batch_fn_k<kLDP>(k, hist);
+#endif
+        default: return nullptr;
+    }
 }
 
 cudaError_t launch_batch_main(int mode, int k, bool hist, int grid, const BatchArgs& a, cudaStream_t s) {

@@ -7,6 +7,7 @@
 #include <cstdint>
 
 #include "ldp.h"
+#include "ldp_modes.h"
 
 namespace ldp {
 
@@ -58,7 +59,13 @@ struct BatchArgs {
     cudaError_t batch_occupancy(int mode, int k, bool hist, int* blocks_per_sm);                          \
     }
 LDP_VARIANTS(LDP_DECLARE_VARIANT)
+// the code-variant modes kLDPRaw, kLDPThresh, kLDPRawThresh (one unit each),
+// in the tile shape of variant 0
+LDP_DECLARE_VARIANT(cm2, 64, 4, 5, 0)
+LDP_DECLARE_VARIANT(cm3, 64, 4, 5, 0)
+LDP_DECLARE_VARIANT(cm4, 64, 4, 5, 0)
 #undef LDP_DECLARE_VARIANT
+constexpr int kCodeModeVariant = 0;  // variant whose tile shape varcm2..4 use
 
 int num_variants();
 const char* variant_name(int v);

@@ -92,26 +92,33 @@ struct SumArgs {
 
 __device__ __forceinline__ int win_count(int n, int w, int s) { return n <= w ? 1 : (n - w + s - 1) / s + 1; }
 
-__global__ void __launch_bounds__(256) k_window_sum(SumArgs a, int count) {
-    for (int img = blockIdx.y; img < count; img += gridDim.y) {
+// One CTA per (window row, image) item, strided over the grid: warps take
+// the row's windows, lanes the bins (consecutive bins: coalesced loads and
+// stores, no division in the loop).
+__global__ void __launch_bounds__(256) k_window_sum(SumArgs a, int count, int nwr_max) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const uint64_t items = (uint64_t)count * (uint64_t)nwr_max;
+    for (uint64_t it = blockIdx.x; it < items; it += gridDim.x) {
+        const int img = (int)(it / (uint64_t)nwr_max), wa = (int)(it % (uint64_t)nwr_max);
         const ldp_image_desc d = a.descs ? a.descs[img] : a.one;
         const int H = d.H, W = d.W;
+        const int nwr = win_count(H, a.wh, a.sh);
+        if (wa >= nwr) continue;
         const int ncr = (H + a.ch - 1) / a.ch, ncc = (W + a.cw - 1) / a.cw;
-        const int nwr = win_count(H, a.wh, a.sh), nwc = win_count(W, a.ww, a.sw);
-        const uint64_t total = (uint64_t)nwr * (uint64_t)nwc * (uint64_t)a.nbins;
+        const int nwc = win_count(W, a.ww, a.sw);
         const uint32_t* cells = a.cells + (uint64_t)img * a.cell_stride;
-        uint32_t* out = a.hist + d.hist_offset;
-        for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-             e += (uint64_t)gridDim.x * blockDim.x) {
-            const int bin = (int)(e % (uint64_t)a.nbins);
-            const uint64_t w = e / (uint64_t)a.nbins;
-            const int wa = (int)(w / (uint64_t)nwc), wb = (int)(w % (uint64_t)nwc);
-            const int i0 = wa * a.sh_c, i1 = min(i0 + a.wh_c, ncr);
+        uint32_t* out = a.hist + d.hist_offset + (uint64_t)wa * (uint64_t)nwc * (uint64_t)a.nbins;
+        const int i0 = wa * a.sh_c, i1 = min(i0 + a.wh_c, ncr);
+        for (int wb = warp; wb < nwc; wb += nwarps) {
             const int j0 = wb * a.sw_c, j1 = min(j0 + a.ww_c, ncc);
-            uint32_t s = 0;
-            for (int ci = i0; ci < i1; ++ci)
-                for (int cj = j0; cj < j1; ++cj) s += cells[((size_t)ci * ncc + cj) * a.nbins + bin];
-            out[e] = s;
+            for (int bin = lane; bin < a.nbins; bin += 32) {
+                uint32_t s = 0;
+                for (int ci = i0; ci < i1; ++ci) {
+                    const uint32_t* row = cells + ((size_t)ci * (size_t)ncc) * (size_t)a.nbins + bin;
+                    for (int cj = j0; cj < j1; ++cj) s += __ldg(row + (size_t)cj * (size_t)a.nbins);
+                }
+                out[(size_t)wb * (size_t)a.nbins + bin] = s;
+            }
         }
     }
 }
@@ -174,12 +181,9 @@ cudaError_t launch_windows(const ldp_image_desc* d_descs, const ldp_image_desc* 
     sa.cells = cells;
     sa.cell_stride = cell_stride;
     sa.hist = hist;
-    const uint64_t total = (uint64_t)((max_H <= g.wh) ? 1 : (max_H - g.wh + g.sh - 1) / g.sh + 1) *
-                           (uint64_t)((max_W <= g.ww) ? 1 : (max_W - g.ww + g.sw - 1) / g.sw + 1) *
-                           (uint64_t)g.nbins;
-    const uint64_t blocks = (total + 255) / 256;
-    dim3 grid2((unsigned)(blocks < 4096 ? blocks : 4096), (unsigned)(count < 65535 ? count : 65535));
-    k_window_sum<<<grid2, 256, 0, s>>>(sa, count);
+    const int nwr_max = (max_H <= g.wh) ? 1 : (max_H - g.wh + g.sh - 1) / g.sh + 1;
+    const uint64_t items = (uint64_t)count * (uint64_t)nwr_max;
+    k_window_sum<<<(unsigned)(items < (1u << 20) ? items : (1u << 20)), 256, 0, s>>>(sa, count, nwr_max);
     return cudaGetLastError();
 }
 

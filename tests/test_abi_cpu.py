@@ -135,3 +135,23 @@ def test_window_host_logic_without_gpu(lib):
                                None) == EINVAL
     assert lib.ldp_batch_window_hist(None, 1, 10, 10, 3, ws, fake, None, 0, None) == EINVAL
     assert lib.ldp_batch_window_hist(fake, 1, 10, 10, 3, ws, fake, None, 0, None) == EINVAL  # no scratch
+
+
+def test_code_mode_arguments_without_gpu(lib):
+    from paper_1810_11518_gb300 import _abi
+
+    EINVAL = _abi.LDP_EINVAL
+    fake = ctypes.c_void_p(0x1000)
+    assert lib.ldp_codes_ex(fake, 10, 10, 10, 3, 4, fake, 8, None) == EINVAL   # no such mode
+    assert lib.ldp_codes_ex(fake, 10, 10, 10, 3, -1, fake, 8, None) == EINVAL
+    assert lib.ldp_codes_ex(fake, 10, 10, 10, 0, 1, fake, 8, None) == EINVAL   # k
+    # threshold modes count raw bins only
+    for m in (_abi.LDP_CODE_ABS_THRESH, _abi.LDP_CODE_RAW_THRESH):
+        assert lib.ldp_region_hist_ex(fake, 10, 10, 10, 3, m, _abi.RegionSpec(2, 2, 1), fake, None, 0,
+                                      None) == EINVAL
+        h = ctypes.c_void_p()
+        assert lib.ldp_batch_plan_create(ctypes.byref(h), 4, 1000, 3, _abi.RegionSpec(2, 2, 1),
+                                         _abi.plan_code_mode(m)) == EINVAL
+    h = ctypes.c_void_p()
+    assert lib.ldp_batch_plan_create(ctypes.byref(h), 4, 1000, 3, _abi.RegionSpec(2, 2, 0),
+                                     _abi.LDP_PLAN_LBP | _abi.plan_code_mode(1)) == EINVAL
