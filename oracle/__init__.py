@@ -70,6 +70,9 @@ def _load():
                                                  vp, i64p, vp, i64p, vp, i32]
             lib.aldp_codes.argtypes = [vp, i32, i32, i32, i32, vp, i32]
             lib.oracle_window_count.argtypes = [i32, i32, i32]
+            lib.oracle_resize_bilinear.argtypes = [vp, i32, i32, i32, i32, i32, i32, i32, vp, i32, i32, i32]
+            lib.oracle_resize_coord.argtypes = [i32, i32, i32, vp, vp]
+            lib.oracle_resize_coord.restype = None
             lib.oracle_window_hist.argtypes = [vp, i32, i32, i32, i32, i32, i32, i32, i32, vp]
             _lib = lib
     return _lib
@@ -229,6 +232,25 @@ def extract_windows(img, k: int = 3, window=(20, 20), stride=None, compact: bool
     cm = codes(img, k=k, mode=mode)
     nbk = k if (mode in (MODE_LDP, MODE_LDP_RAW) and compact) else 0
     return window_hist(cm, H, W, window[0], window[1], stride[0], stride[1], nbk), cm
+
+
+def resize_coord(i: int, n_src: int, n_dst: int) -> tuple[int, int]:
+    a, b = ctypes.c_int(), ctypes.c_int()
+    _load().oracle_resize_coord(i, n_src, n_dst, ctypes.byref(a), ctypes.byref(b))
+    return a.value, b.value
+
+
+def resize(img, out_hw=(260, 260), crop=None) -> np.ndarray:
+    """Bilinear crop-and-resize (Sec. 3.1 front end); crop = (y, x, h, w), default the whole image."""
+    img = _u8(img)
+    H, W = img.shape
+    cy, cx, ch, cw = (0, 0, H, W) if crop is None else crop
+    OH, OW = out_hw
+    out = np.zeros((OH, OW), dtype=np.uint8)
+    rc = _load().oracle_resize_bilinear(img.ctypes.data, H, W, W, cy, cx, ch, cw, out.ctypes.data, OH, OW, OW)
+    if rc:
+        raise ValueError("oracle_resize_bilinear rejected the arguments")
+    return out
 
 
 def extract(img, k: int = 3, R: int = 1, C: int = 1, compact: bool = True, mode: int = MODE_LDP,

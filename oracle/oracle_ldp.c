@@ -238,6 +238,56 @@ int oracle_window_hist(const uint8_t *codes, int H, int W, int code_pitch, int w
     return 0;
 }
 
+/* Sample position of output index i: y = ((2i + 1) n_src - n_dst) / (2 n_dst)
+ * exactly; i0 = floor(y), w1 = round((y - i0) * 2048) with halves up;
+ * y < 0 clamps to (0, 0) and y >= n_src - 1 to (n_src - 1, 0). */
+void oracle_resize_coord(int i, int n_src, int n_dst, int *i0, int *w1) {
+    const long long num = (2LL * i + 1) * (long long)n_src - (long long)n_dst;  /* y * 2 n_dst */
+    const long long den = 2LL * n_dst;
+    if (num <= 0) {
+        *i0 = 0;
+        *w1 = 0;
+        return;
+    }
+    long long q = num / den, r = num - q * den;
+    long long w = (r * 2048 + den / 2) / den;  /* round half up (den is even) */
+    if (w == 2048) {
+        q += 1;
+        w = 0;
+    }
+    if (q >= n_src - 1) {
+        *i0 = n_src - 1;
+        *w1 = 0;
+        return;
+    }
+    *i0 = (int)q;
+    *w1 = (int)w;
+}
+
+int oracle_resize_bilinear(const uint8_t *src, int H, int W, int pitch, int cy, int cx, int ch, int cw,
+                           uint8_t *dst, int OH, int OW, int dst_pitch) {
+    if (!src || !dst || H < 1 || W < 1 || pitch < W || ch < 1 || cw < 1 || OH < 1 || OW < 1 || dst_pitch < OW)
+        return -1;
+    if (cy < 0 || cx < 0 || cy + ch > H || cx + cw > W) return -1;
+    for (int i = 0; i < OH; ++i) {
+        int y0, wy1;
+        oracle_resize_coord(i, ch, OH, &y0, &wy1);
+        const int y1 = (y0 + 1 < ch) ? y0 + 1 : y0, wy0 = 2048 - wy1;
+        for (int j = 0; j < OW; ++j) {
+            int x0, wx1;
+            oracle_resize_coord(j, cw, OW, &x0, &wx1);
+            const int x1 = (x0 + 1 < cw) ? x0 + 1 : x0, wx0 = 2048 - wx1;
+            const long long p00 = src[(size_t)(cy + y0) * pitch + (size_t)(cx + x0)];
+            const long long p01 = src[(size_t)(cy + y0) * pitch + (size_t)(cx + x1)];
+            const long long p10 = src[(size_t)(cy + y1) * pitch + (size_t)(cx + x0)];
+            const long long p11 = src[(size_t)(cy + y1) * pitch + (size_t)(cx + x1)];
+            const long long v = wy0 * (wx0 * p00 + wx1 * p01) + wy1 * (wx0 * p10 + wx1 * p11);
+            dst[(size_t)i * dst_pitch + (size_t)j] = (uint8_t)((v + (1LL << 21)) >> 22);
+        }
+    }
+    return 0;
+}
+
 int oracle_extract(const uint8_t *img, int H, int W, int pitch, int mode, int k, int R, int C,
                    int compact, uint32_t *hist, uint8_t *codes, int code_pitch) {
     if (!img || H < 3 || W < 3 || pitch < W) return -1;

@@ -94,6 +94,23 @@ int oracle_window_count(int n, int w, int s);
 int oracle_window_hist(const uint8_t *codes, int H, int W, int code_pitch, int wh, int ww, int sh,
                        int sw, int nbins_k, uint32_t *hist);
 
+/* Crop-and-resize front end (Sec. 3.1: faces resized to 260 x 260).
+ * Bilinear resampling of the crop rectangle (rows cy..cy+ch-1, columns
+ * cx..cx+cw-1 of the source) to OH x OW with half-pixel centres: output
+ * pixel (i, j) samples the crop at y = (i + 1/2) * ch / OH - 1/2,
+ * x = (j + 1/2) * cw / OW - 1/2, clamped to [0, ch-1] x [0, cw-1].  The
+ * fraction of each coordinate is quantised to an 11-bit weight w1 =
+ * round(frac * 2048) (halves up), w0 = 2048 - w1, all in exact integer
+ * arithmetic on the rational coordinate, and
+ *   out = (wy0 (wx0 p00 + wx1 p01) + wy1 (wx0 p10 + wx1 p11) + 2^21) >> 22.
+ * Returns -1 on invalid arguments. */
+int oracle_resize_bilinear(const uint8_t *src, int H, int W, int pitch, int cy, int cx, int ch, int cw,
+                           uint8_t *dst, int OH, int OW, int dst_pitch);
+
+/* The integer sampling position of output index i along an axis (the rule
+ * above): first source index and the 11-bit weight of the next one. */
+void oracle_resize_coord(int i, int n_src, int n_dst, int *i0, int *w1);
+
 /* Whole path for one image: codes (optional, may be NULL) + region hists.
  * mode as oracle_codes_rect; compact selects C(8,k) bins for the exact-k
  * LDP modes 0 and 2 (the threshold modes always count 256 raw bins). */
