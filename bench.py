@@ -279,6 +279,59 @@ def time_windows(ldp, torch, dev, n, H, W, k, window, stride, steps):
             "window_pass_ms": round(tw / steps, 4)}
 
 
+def time_face_pipeline(ldp, torch, dev, lay, d_img, k, steps, seed=7):
+    """The paper's front end on resident frames (Sec. 3.1-3.2): one seeded
+    crop box per frame resized to 260 x 260 in one launch, one persistent
+    LDP launch over the crops (codes), their 20 x 20 window histograms
+    (13 x 13 windows, Table 3's geometry).  Each stage is timed with CUDA
+    events on the current stream."""
+    n = lay.n
+    rng = np.random.default_rng(seed)
+    OH = OW = 260
+    crops = np.zeros(n, dtype=ldp.CROP_DTYPE)
+    faces = ldp.BatchLayout.build([OH] * n, [OW] * n, hist_len=0)
+    d_faces = torch.empty(faces.img_bytes, dtype=torch.uint8, device=dev)
+    d_fcodes = torch.empty(faces.code_bytes, dtype=torch.uint8, device=dev)
+    for i in range(n):
+        H, W = int(lay.Hs[i]), int(lay.Ws[i])
+        s = int(rng.integers(180, min(H, W) + 1))
+        cy, cx = int(rng.integers(0, H - s + 1)), int(rng.integers(0, W - s + 1))
+        crops[i] = (d_img.data_ptr() + int(lay.img_off[i]), d_faces.data_ptr() + int(faces.img_off[i]), H, W,
+                    int(lay.pitches[i]), cy, cx, s, s, int(faces.pitches[i]))
+    d_crops = torch.from_numpy(crops.view(np.uint8)).to(dev)
+    win = (20, 20)
+    nwin = ldp.window_count(OH, 20, 20) * ldp.window_count(OW, 20, 20)
+    per = nwin * ldp.hist_bins(k)
+    descs = faces.descs(d_faces.data_ptr(), d_fcodes.data_ptr())
+    descs["hist_offset"] = np.arange(n, dtype=np.uint64) * np.uint64(per)
+    d_desc = torch.from_numpy(descs.view(np.uint8)).to(dev)
+    d_count = torch.tensor([n], dtype=torch.int32, device=dev)
+    d_hist = torch.empty(n * per, dtype=torch.int32, device=dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    t = np.zeros(3)
+    with ldp.BatchPlan(n, faces.pixels, k=k, regions=(1, 1)) as plan:
+        for it in range(3 + steps):
+            ev[0].record()
+            ldp.batch_resize(d_crops, n, (OH, OW))
+            ev[1].record()
+            plan.run(d_desc, d_count, None)
+            ev[2].record()
+            ldp.batch_window_hist(d_desc, n, (OH, OW), k, win, None, hist=d_hist)
+            ev[3].record()
+            torch.cuda.synchronize(dev)
+            if it >= 3:
+                t += [ev[j].elapsed_time(ev[j + 1]) for j in range(3)]
+    t /= steps
+    ms = float(t.sum())
+    if ldp.device_status() != 0:
+        raise RuntimeError("a crop or batch descriptor was rejected")
+    return {"faces": n, "face": [OH, OW], "k": k, "window": list(win), "windows_per_face": nwin,
+            "ms_per_step": round(ms, 4), "faces_per_s": round(n / (ms * 1e-3), 1),
+            "value": round(faces.pixels / (ms * 1e-3) / 1e6, 3), "unit": "Mpixel/s of 260x260 faces",
+            "stage_ms": {"resize": round(float(t[0]), 4), "ldp_codes": round(float(t[1]), 4),
+                         "windows": round(float(t[2]), 4)}}
+
+
 def run_reference(a):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -489,6 +542,7 @@ def main():
     if not a.no_extras and rank == 0:
         # Table 3 windows on the paper's 260 x 260 face crops, and overlapping
         # windows (stride half the size) on the 640 x 490 batch
+        extras["face_pipeline"] = time_face_pipeline(ldp, torch, dev, lay, d_img, k, max(5, a.steps // 10))
         extras["windows"] = [
             time_windows(ldp, torch, dev, 4096, 260, 260, k, (20, 20), None, max(5, a.steps // 10)),
             time_windows(ldp, torch, dev, 4096, 490, 640, k, (20, 20), (10, 10), max(5, a.steps // 10)),

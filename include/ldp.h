@@ -113,6 +113,35 @@ LDP_API int lbp_codes(const uint8_t *d_img, int H, int W, int pitch, uint8_t *d_
 LDP_API int lbp_region_hist(const uint8_t *d_img, int H, int W, int pitch, int R, int C, uint32_t *d_hist,
                     uint8_t *d_codes_or_null, int code_pitch, void *stream);
 
+/* ---- crop-and-resize front end (Sec. 3.1) ---- */
+
+/* One crop of a batch: rows cy..cy+ch-1, columns cx..cx+cw-1 of the source
+ * image (H x W, row pitch `pitch`), resized into dst (row pitch dst_pitch).
+ * 48 bytes, 8-byte aligned. */
+typedef struct {
+    const uint8_t *src;
+    uint8_t *dst;
+    int32_t H, W, pitch;
+    int32_t cy, cx, ch, cw;
+    int32_t dst_pitch;
+} ldp_crop_desc;
+
+/* Bilinear crop-and-resize (the paper resizes detected faces to 260 x 260
+ * before extraction; detection itself is not part of the library): output
+ * pixel (i, j) samples the crop at ((i + 1/2) ch / OH - 1/2,
+ * (j + 1/2) cw / OW - 1/2), clamped to the crop; the fractions become 11-bit
+ * weights (round half up) computed in exact integer arithmetic, and the
+ * result is (sum of weight products x pixels + 2^21) >> 22.  d_dst: OH x OW,
+ * row pitch dst_pitch >= OW.  EINVAL: NULL pointers, the crop outside the
+ * image, sizes < 1, pitch < W, dst_pitch < OW, OH or OW > 1<<16. */
+LDP_API int ldp_resize(const uint8_t *d_src, int H, int W, int pitch, int cy, int cx, int ch, int cw,
+                       uint8_t *d_dst, int OH, int OW, int dst_pitch, void *stream);
+
+/* Every crop of d_descs[0..count) (device memory, count a host value) to
+ * OH x OW in one launch.  A descriptor that fails the checks of ldp_resize
+ * is skipped and sets bit 3 of the device status word (ldp_device_status). */
+LDP_API int ldp_batch_resize(const ldp_crop_desc *d_descs, int count, int OH, int OW, void *stream);
+
 /* ---- readings of Eq. 2-3 (code modes) ----
  * Eq. 2 sets s(m_i - m_k) for the k-th "most outstanding" response; the
  * printed formula leaves the ranking (|m_i| or m_i) and the treatment of ties
@@ -348,7 +377,9 @@ LDP_API int ldp_bin_of_code(int code, int k);
 LDP_API const char *ldp_last_error(void);
 
 /* Reads and clears the device status word (bit 0: a batch descriptor was
- * rejected on the device).  Synchronises `stream`. */
+ * rejected on the device; bit 1: a batch needed more tiles than its plan
+ * holds; bit 2: a bounded wait for staged input gave up; bit 3: a crop
+ * descriptor was rejected).  Synchronises `stream`. */
 LDP_API int ldp_device_status(void *stream, int *out);
 
 /* Library version (major*10000 + minor*100 + patch). */

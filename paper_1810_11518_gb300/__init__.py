@@ -23,11 +23,16 @@ from ._abi import LdpError, RegionSpec, WindowSpec
 __all__ = ["codes", "region_hist", "lbp_codes", "lbp_region_hist", "hist_bins", "bin_of_code",
            "BatchPlan", "BatchLayout", "DESC_DTYPE", "LdpError", "device_status", "num_variants",
            "variant_name", "set_plain_variant", "load", "batch_run_noalloc", "window_count", "window_hist",
-           "lbp_window_hist", "batch_window_hist", "CODE_ABS", "CODE_RAW", "CODE_ABS_THRESH", "CODE_RAW_THRESH"]
+           "lbp_window_hist", "batch_window_hist", "resize", "batch_resize", "CROP_DTYPE", "CODE_ABS", "CODE_RAW", "CODE_ABS_THRESH", "CODE_RAW_THRESH"]
 
 DESC_DTYPE = np.dtype([("img", "<u8"), ("H", "<i4"), ("W", "<i4"), ("pitch", "<i4"),
                        ("code_pitch", "<i4"), ("codes", "<u8"), ("hist_offset", "<u8")])
 assert DESC_DTYPE.itemsize == 40
+
+# ldp_crop_desc: one crop of a batch resize (include/ldp.h)
+CROP_DTYPE = np.dtype([("src", "<u8"), ("dst", "<u8"), ("H", "<i4"), ("W", "<i4"), ("pitch", "<i4"),
+                       ("cy", "<i4"), ("cx", "<i4"), ("ch", "<i4"), ("cw", "<i4"), ("dst_pitch", "<i4")])
+assert CROP_DTYPE.itemsize == 48
 
 
 def load():
@@ -216,6 +221,29 @@ def batch_window_hist(d_descs, count: int, max_hw, k: int, window, stride=None, 
     if scratch is not None:
         scratch.record_stream(torch.cuda.current_stream() if stream is None else stream)
     return hist
+
+
+def resize(img, out_hw=(260, 260), crop=None, out=None, stream=None):
+    """Bilinear crop-and-resize (Sec. 3.1 front end: faces resized to 260 x 260).
+    crop = (y, x, h, w) of the source (default: all of it).  Returns uint8 (OH, OW)."""
+    torch = _torch()
+    p, H, W, P = _img(img)
+    cy, cx, ch, cw = (0, 0, H, W) if crop is None else crop
+    OH, OW = out_hw
+    if out is None:
+        out = torch.empty((OH, OW), dtype=torch.uint8, device=img.device)
+    elif out.dtype != torch.uint8 or out.dim() != 2 or tuple(out.shape) != (OH, OW) or out.stride(1) != 1:
+        raise ValueError(f"out must be a uint8 tensor of shape {(OH, OW)} with unit column stride")
+    _abi.call("ldp_resize", p, H, W, P, cy, cx, ch, cw, ctypes.c_void_p(out.data_ptr()), OH, OW,
+              int(out.stride(0)), _stream(stream))
+    return out
+
+
+def batch_resize(d_descs, count: int, out_hw=(260, 260), stream=None) -> None:
+    """Every crop of `d_descs` (a CUDA tensor of CROP_DTYPE records) resized to out_hw in one launch;
+    rejected descriptors are skipped and reported by device_status() (bit 3)."""
+    _abi.call("ldp_batch_resize", ctypes.c_void_p(d_descs.data_ptr()), int(count), int(out_hw[0]),
+              int(out_hw[1]), _stream(stream))
 
 
 def num_variants() -> int:

@@ -38,6 +38,7 @@ EXPORTS = [
     "ldp_server_create", "ldp_server_submit", "ldp_server_poll", "ldp_server_stats", "ldp_server_destroy",
     "ldp_window_count", "ldp_window_scratch_bytes", "ldp_window_hist", "lbp_window_hist",
     "ldp_batch_window_scratch_bytes", "ldp_batch_window_hist", "ldp_codes_ex", "ldp_region_hist_ex",
+    "ldp_resize", "ldp_batch_resize",
 ]
 
 
@@ -124,6 +125,8 @@ def load(path: str | None = None):
             "ldp_server_destroy": [vp],
             "ldp_window_count": [i32, i32, i32],
             "ldp_codes_ex": [vp, i32, i32, i32, i32, i32, vp, i32, vp],
+            "ldp_resize": [vp, i32, i32, i32, i32, i32, i32, i32, vp, i32, i32, i32, vp],
+            "ldp_batch_resize": [vp, i32, i32, i32, vp],
             "ldp_region_hist_ex": [vp, i32, i32, i32, i32, i32, RegionSpec, vp, vp, i32, vp],
             "ldp_window_scratch_bytes": [i32, i32, i32, WindowSpec, i32],
             "ldp_window_hist": [vp, i32, i32, i32, i32, WindowSpec, vp, vp, i32, vp, u64, vp],

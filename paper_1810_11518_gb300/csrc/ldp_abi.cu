@@ -214,6 +214,34 @@ int ldp_region_hist_ex(const uint8_t* d_img, int H, int W, int pitch, int k, int
                      stream);
 }
 
+int ldp_resize(const uint8_t* d_src, int H, int W, int pitch, int cy, int cx, int ch, int cw, uint8_t* d_dst,
+               int OH, int OW, int dst_pitch, void* stream) {
+    if (!d_src || !d_dst) return fail(LDP_EINVAL, "image pointer is NULL");
+    if (H < 1 || W < 1 || pitch < W) return fail(LDP_EINVAL, "bad source size or pitch");
+    if (H > (1 << 20) || W > (1 << 20)) return fail(LDP_EINVAL, "image side larger than 1<<20");
+    if (ch < 1 || cw < 1 || cy < 0 || cx < 0 || cy + ch > H || cx + cw > W)
+        return fail(LDP_EINVAL, "crop outside the image");
+    if (OH < 1 || OW < 1 || OH > (1 << 16) || OW > (1 << 16)) return fail(LDP_EINVAL, "output size out of range");
+    if (dst_pitch < OW) return fail(LDP_EINVAL, "dst_pitch < OW");
+    int* status = ldp::status_word();
+    if (!status) return fail(LDP_ECUDA, "device status word not found");
+    ldp_crop_desc one{d_src, d_dst, H, W, pitch, cy, cx, ch, cw, dst_pitch};
+    cudaError_t e = ldp::launch_resize(nullptr, &one, 1, OH, OW, status, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "resize kernel");
+    return LDP_OK;
+}
+
+int ldp_batch_resize(const ldp_crop_desc* d_descs, int count, int OH, int OW, void* stream) {
+    if (!d_descs) return fail(LDP_EINVAL, "descriptor pointer is NULL");
+    if (count < 1 || count > (1 << 24)) return fail(LDP_EINVAL, "count must be in [1, 1<<24]");
+    if (OH < 1 || OW < 1 || OH > (1 << 16) || OW > (1 << 16)) return fail(LDP_EINVAL, "output size out of range");
+    int* status = ldp::status_word();
+    if (!status) return fail(LDP_ECUDA, "device status word not found");
+    cudaError_t e = ldp::launch_resize(d_descs, nullptr, count, OH, OW, status, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "resize kernel");
+    return LDP_OK;
+}
+
 int ldp_window_count(int n, int w, int s) {
     if (w < 1 || s < 1 || n < 0) return -1;
     return n <= w ? 1 : (n - w + s - 1) / s + 1;

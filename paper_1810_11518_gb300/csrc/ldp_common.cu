@@ -12,7 +12,7 @@ namespace ldp {
 
 // Device status word: bit 0 = a batch descriptor was rejected on the device,
 // bit 1 = a batch needed more tiles than its plan holds, bit 2 = a bounded
-// wait for staged input gave up.
+// wait for staged input gave up, bit 3 = a crop descriptor was rejected.
 __device__ int g_status;
 
 int* status_word() {

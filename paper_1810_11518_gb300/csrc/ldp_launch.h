@@ -100,6 +100,11 @@ cudaError_t launch_windows(const ldp_image_desc* d_descs, const ldp_image_desc* 
                            int max_W, const WindowGeom& g, uint32_t* hist, uint32_t* cells,
                            uint64_t cell_stride, cudaStream_t s);
 
+// Crop-and-resize (ldp_resize.cu): descriptors in device memory (d_descs) or
+// one by value (one, count = 1); rejected crops set status bit 3.
+cudaError_t launch_resize(const ldp_crop_desc* d_descs, const ldp_crop_desc* one, int count, int OH, int OW,
+                          int* status, cudaStream_t s);
+
 cudaError_t read_clear_status(cudaStream_t s, int* out);
 // Device address of the status word on the current device (looked up once per device).
 int* status_word();

@@ -1,0 +1,112 @@
+// Crop-and-resize front end (Sec. 3.1: detected faces are resized to
+// 260 x 260 before extraction).  Bilinear resampling with half-pixel centres:
+// output index i of an axis samples the source at
+//     y = ((2i + 1) n_src - n_dst) / (2 n_dst),
+// clamped to [0, n_src - 1]; the fraction becomes an 11-bit weight
+// w1 = round(frac * 2048) (halves up), w0 = 2048 - w1, all in exact integer
+// arithmetic, and
+//     out = (wy0 (wx0 p00 + wx1 p01) + wy1 (wx0 p10 + wx1 p11) + 2^21) >> 22
+// (at most 2048 * 2048 * 255 + 2^21 < 2^32).  A CTA owns kRows output rows of
+// one image: the rows' coordinates are computed once into shared memory,
+// each thread owns output columns (coalesced stores) and their coordinates.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "ldp_launch.h"
+
+namespace ldp {
+
+namespace {
+
+constexpr int kRows = 16;
+constexpr int kThreads = 256;
+constexpr int kStatusBadCrop = 8;  // device status bit: a crop descriptor was rejected
+
+__device__ __forceinline__ void coord(int i, int n_src, int n_dst, int& i0, int& w1) {
+    const long long num = (2LL * i + 1) * (long long)n_src - (long long)n_dst;
+    const long long den = 2LL * n_dst;
+    if (num <= 0) {
+        i0 = 0;
+        w1 = 0;
+        return;
+    }
+    long long q = num / den;
+    const long long r = num - q * den;
+    long long w = (r * 2048 + den / 2) / den;
+    if (w == 2048) {
+        q += 1;
+        w = 0;
+    }
+    if (q >= n_src - 1) {
+        i0 = n_src - 1;
+        w1 = 0;
+        return;
+    }
+    i0 = (int)q;
+    w1 = (int)w;
+}
+
+struct ResizeArgs {
+    const ldp_crop_desc* descs;  // nullptr: the single crop `one`
+    ldp_crop_desc one;
+    int count, OH, OW;
+    int* status;
+};
+
+__global__ void __launch_bounds__(kThreads) k_resize(ResizeArgs a) {
+    __shared__ int s_y0[kRows], s_y1[kRows], s_wy1[kRows];
+    const int r0 = blockIdx.x * kRows;
+    for (int img = blockIdx.y; img < a.count; img += gridDim.y) {
+        const ldp_crop_desc d = a.descs ? a.descs[img] : a.one;
+        const bool ok = d.src && d.dst && d.ch >= 1 && d.cw >= 1 && d.cy >= 0 && d.cx >= 0 &&
+                        d.cy + d.ch <= d.H && d.cx + d.cw <= d.W && d.pitch >= d.W && d.dst_pitch >= a.OW;
+        if (!ok) {  // uniform over the CTA
+            if (threadIdx.x == 0 && blockIdx.x == 0) atomicOr(a.status, kStatusBadCrop);
+            continue;
+        }
+        __syncthreads();  // the previous image's row table is no longer read
+        if (threadIdx.x < kRows && r0 + (int)threadIdx.x < a.OH) {
+            int y0, w;
+            coord(r0 + threadIdx.x, d.ch, a.OH, y0, w);
+            s_y0[threadIdx.x] = d.cy + y0;
+            s_y1[threadIdx.x] = d.cy + (y0 + 1 < d.ch ? y0 + 1 : y0);
+            s_wy1[threadIdx.x] = w;
+        }
+        __syncthreads();
+        const int nr = min(kRows, a.OH - r0);
+        for (int j = threadIdx.x; j < a.OW; j += blockDim.x) {
+            int x0, wx1;
+            coord(j, d.cw, a.OW, x0, wx1);
+            const int xa = d.cx + x0, xb = d.cx + (x0 + 1 < d.cw ? x0 + 1 : x0);
+            const uint32_t wx0 = 2048u - (uint32_t)wx1;
+            for (int r = 0; r < nr; ++r) {
+                const uint8_t* pa = d.src + (size_t)s_y0[r] * (size_t)d.pitch;
+                const uint8_t* pb = d.src + (size_t)s_y1[r] * (size_t)d.pitch;
+                const uint32_t top = wx0 * __ldg(pa + xa) + (uint32_t)wx1 * __ldg(pa + xb);
+                const uint32_t bot = wx0 * __ldg(pb + xa) + (uint32_t)wx1 * __ldg(pb + xb);
+                const uint32_t wy1 = (uint32_t)s_wy1[r];
+                const uint32_t v = (2048u - wy1) * top + wy1 * bot;
+                d.dst[(size_t)(r0 + r) * (size_t)d.dst_pitch + j] = (uint8_t)((v + (1u << 21)) >> 22);
+            }
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_resize(const ldp_crop_desc* d_descs, const ldp_crop_desc* one, int count, int OH, int OW,
+                          int* status, cudaStream_t s) {
+    ResizeArgs a{};
+    a.descs = d_descs;
+    if (one) a.one = *one;
+    a.count = count;
+    a.OH = OH;
+    a.OW = OW;
+    a.status = status;
+    dim3 grid((OH + kRows - 1) / kRows, count < 65535 ? count : 65535);
+    k_resize<<<grid, kThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace ldp

@@ -155,3 +155,27 @@ def test_code_mode_arguments_without_gpu(lib):
     h = ctypes.c_void_p()
     assert lib.ldp_batch_plan_create(ctypes.byref(h), 4, 1000, 3, _abi.RegionSpec(2, 2, 0),
                                      _abi.LDP_PLAN_LBP | _abi.plan_code_mode(1)) == EINVAL
+
+
+def test_resize_arguments_without_gpu(lib):
+    import paper_1810_11518_gb300 as ldp
+    from paper_1810_11518_gb300 import _abi
+
+    EINVAL = _abi.LDP_EINVAL
+    fake = ctypes.c_void_p(0x1000)
+    assert ldp.CROP_DTYPE.itemsize == 48
+    ok = (fake, 100, 120, 128, 10, 20, 50, 60, fake, 26, 26, 26, None)
+    bad = [
+        (None,) + ok[1:],
+        ok[:4] + (-1,) + ok[5:],             # crop above the image
+        ok[:4] + (60, 20, 50, 60) + ok[8:],  # crop past the bottom
+        ok[:6] + (0,) + ok[7:],              # empty crop
+        ok[:3] + (119,) + ok[4:],            # pitch < W
+        ok[:9] + (0,) + ok[10:],             # OH
+        ok[:11] + (25, None),                # dst_pitch < OW
+    ]
+    for args in bad:
+        assert lib.ldp_resize(*args) == EINVAL, args
+    assert lib.ldp_batch_resize(None, 1, 26, 26, None) == EINVAL
+    assert lib.ldp_batch_resize(fake, 0, 26, 26, None) == EINVAL
+    assert lib.ldp_batch_resize(fake, 1, 0, 26, None) == EINVAL
