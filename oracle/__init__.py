@@ -73,6 +73,7 @@ def _load():
             lib.oracle_resize_bilinear.argtypes = [vp, i32, i32, i32, i32, i32, i32, i32, vp, i32, i32, i32]
             lib.oracle_resize_coord.argtypes = [i32, i32, i32, vp, vp]
             lib.oracle_resize_coord.restype = None
+            lib.oracle_hist_distance.argtypes = [vp, i32, i32, vp, i32, i32, i32, i32, vp, i32]
             lib.oracle_window_hist.argtypes = [vp, i32, i32, i32, i32, i32, i32, i32, i32, vp]
             _lib = lib
     return _lib
@@ -232,6 +233,23 @@ def extract_windows(img, k: int = 3, window=(20, 20), stride=None, compact: bool
     cm = codes(img, k=k, mode=mode)
     nbk = k if (mode in (MODE_LDP, MODE_LDP_RAW) and compact) else 0
     return window_hist(cm, H, W, window[0], window[1], stride[0], stride[1], nbk), cm
+
+
+DIST_L1, DIST_INTERSECT, DIST_CHI2 = 0, 1, 2
+
+
+def hist_distance(q, g, metric: int = DIST_CHI2) -> np.ndarray:
+    """(nq, ng) distances between descriptor rows: uint64 for L1 / intersection, float64 for chi-square."""
+    q = np.ascontiguousarray(q, dtype=np.uint32).reshape(len(q), -1)
+    g = np.ascontiguousarray(g, dtype=np.uint32).reshape(len(g), -1)
+    if q.shape[1] != g.shape[1]:
+        raise ValueError("descriptor lengths differ")
+    out = np.zeros((q.shape[0], g.shape[0]), dtype=np.float64 if metric == DIST_CHI2 else np.uint64)
+    rc = _load().oracle_hist_distance(q.ctypes.data, q.shape[0], q.shape[1], g.ctypes.data, g.shape[0],
+                                      g.shape[1], q.shape[1], metric, out.ctypes.data, g.shape[0])
+    if rc:
+        raise ValueError("oracle_hist_distance rejected the arguments")
+    return out
 
 
 def resize_coord(i: int, n_src: int, n_dst: int) -> tuple[int, int]:

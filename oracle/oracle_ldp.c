@@ -288,6 +288,27 @@ int oracle_resize_bilinear(const uint8_t *src, int H, int W, int pitch, int cy, 
     return 0;
 }
 
+int oracle_hist_distance(const uint32_t *q, int nq, int ldq, const uint32_t *g, int ng, int ldg, int D,
+                         int metric, void *out, int ldo) {
+    if (!q || !g || !out || nq < 1 || ng < 1 || D < 1 || ldq < D || ldg < D || ldo < ng) return -1;
+    if (metric < 0 || metric > 2) return -1;
+    for (int a = 0; a < nq; ++a)
+        for (int b = 0; b < ng; ++b) {
+            const uint32_t *x = q + (size_t)a * ldq, *y = g + (size_t)b * ldg;
+            uint64_t acc = 0;
+            double chi = 0.0;
+            for (int d = 0; d < D; ++d) {
+                const uint64_t u = x[d], v = y[d];
+                if (metric == 0) acc += u > v ? u - v : v - u;
+                else if (metric == 1) acc += u < v ? u : v;
+                else if (u + v > 0) chi += ((double)u - (double)v) * ((double)u - (double)v) / ((double)u + (double)v);
+            }
+            if (metric == 2) ((double *)out)[(size_t)a * ldo + b] = chi;
+            else ((uint64_t *)out)[(size_t)a * ldo + b] = acc;
+        }
+    return 0;
+}
+
 int oracle_extract(const uint8_t *img, int H, int W, int pitch, int mode, int k, int R, int C,
                    int compact, uint32_t *hist, uint8_t *codes, int code_pitch) {
     if (!img || H < 3 || W < 3 || pitch < W) return -1;

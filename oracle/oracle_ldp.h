@@ -111,6 +111,17 @@ int oracle_resize_bilinear(const uint8_t *src, int H, int W, int pitch, int cy, 
  * above): first source index and the 11-bit weight of the next one. */
 void oracle_resize_coord(int i, int n_src, int n_dst, int *i0, int *w1);
 
+/* Distances between LDP descriptors (histograms used as feature vectors,
+ * Sec. 3.2-3.3): for query rows q_a (nq x D, row stride ldq) and gallery rows
+ * g_b (ng x D, row stride ldg),
+ *   metric 0 (L1):            sum_d |q - g|
+ *   metric 1 (intersection):  sum_d min(q, g)
+ *   metric 2 (chi-square):    sum over d with q + g > 0 of (q - g)^2 / (q + g)
+ * out[a * ldo + b]: uint64 for metrics 0 and 1, double for metric 2.
+ * Returns -1 on invalid arguments. */
+int oracle_hist_distance(const uint32_t *q, int nq, int ldq, const uint32_t *g, int ng, int ldg, int D,
+                         int metric, void *out, int ldo);
+
 /* Whole path for one image: codes (optional, may be NULL) + region hists.
  * mode as oracle_codes_rect; compact selects C(8,k) bins for the exact-k
  * LDP modes 0 and 2 (the threshold modes always count 256 raw bins). */
