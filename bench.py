@@ -332,6 +332,30 @@ def time_face_pipeline(ldp, torch, dev, lay, d_img, k, steps, seed=7):
                          "windows": round(float(t[2]), 4)}}
 
 
+def time_distances(ldp, torch, dev, d_hist, n, hist_len, steps):
+    """Matching leg: every metric between the n descriptors of the main leg
+    (n x n pairs of hist_len-component region histograms)."""
+    desc = d_hist.view(n, hist_len)
+    out = {}
+    for name, metric in (("l1", ldp.DIST_L1), ("intersection", ldp.DIST_INTERSECT), ("chi2", ldp.DIST_CHI2)):
+        res = ldp.hist_distance(desc, desc, metric)
+        for _ in range(2):
+            ldp.hist_distance(desc, desc, metric, out=res)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e0.record()
+        for _ in range(steps):
+            ldp.hist_distance(desc, desc, metric, out=res)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / steps
+        comps = float(n) * n * hist_len
+        out[name] = {"ms": round(ms, 4), "pairs_per_s": round(n * n / (ms * 1e-3), 1),
+                     "g_components_per_s": round(comps / (ms * 1e-3) / 1e9, 1)}
+        del res
+    return {"queries": n, "gallery": n, "components": hist_len, "metrics": out}
+
+
 def run_reference(a):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -542,6 +566,7 @@ def main():
     if not a.no_extras and rank == 0:
         # Table 3 windows on the paper's 260 x 260 face crops, and overlapping
         # windows (stride half the size) on the 640 x 490 batch
+        extras["distances"] = time_distances(ldp, torch, dev, d_hist, n, hist_len, 5)
         extras["face_pipeline"] = time_face_pipeline(ldp, torch, dev, lay, d_img, k, max(5, a.steps // 10))
         extras["windows"] = [
             time_windows(ldp, torch, dev, 4096, 260, 260, k, (20, 20), None, max(5, a.steps // 10)),

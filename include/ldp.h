@@ -142,6 +142,22 @@ LDP_API int ldp_resize(const uint8_t *d_src, int H, int W, int pitch, int cy, in
  * is skipped and sets bit 3 of the device status word (ldp_device_status). */
 LDP_API int ldp_batch_resize(const ldp_crop_desc *d_descs, int count, int OH, int OW, void *stream);
 
+/* ---- distances between descriptors (matching LDP feature vectors) ---- */
+
+#define LDP_DIST_L1 0        /* sum |q - g|, uint64 out */
+#define LDP_DIST_INTERSECT 1 /* sum min(q, g), uint64 out */
+#define LDP_DIST_CHI2 2      /* sum over q + g > 0 of (q - g)^2 / (q + g), float out */
+
+/* Distance of every query row (d_q: nq x D uint32, row stride ldq) to every
+ * gallery row (d_g: ng x D, row stride ldg), e.g. region or window
+ * histograms of images: d_out[a * ldo + b] (uint64 for L1 / intersection,
+ * float for chi-square).  Integer metrics are exact for counts below 2^27;
+ * chi-square runs in fp32 (counts exact below 2^24): relative error at most
+ * (D + 5) * 2^-24 (every term is non-negative).  EINVAL: NULL pointers,
+ * nq, ng or D < 1, ldq < D, ldg < D, ldo < ng, unknown metric. */
+LDP_API int ldp_hist_distance(const uint32_t *d_q, int nq, int ldq, const uint32_t *d_g, int ng, int ldg, int D,
+                              int metric, void *d_out, int ldo, void *stream);
+
 /* ---- readings of Eq. 2-3 (code modes) ----
  * Eq. 2 sets s(m_i - m_k) for the k-th "most outstanding" response; the
  * printed formula leaves the ranking (|m_i| or m_i) and the treatment of ties

@@ -23,7 +23,8 @@ from ._abi import LdpError, RegionSpec, WindowSpec
 __all__ = ["codes", "region_hist", "lbp_codes", "lbp_region_hist", "hist_bins", "bin_of_code",
            "BatchPlan", "BatchLayout", "DESC_DTYPE", "LdpError", "device_status", "num_variants",
            "variant_name", "set_plain_variant", "load", "batch_run_noalloc", "window_count", "window_hist",
-           "lbp_window_hist", "batch_window_hist", "resize", "batch_resize", "CROP_DTYPE", "CODE_ABS", "CODE_RAW", "CODE_ABS_THRESH", "CODE_RAW_THRESH"]
+           "lbp_window_hist", "batch_window_hist", "resize", "batch_resize", "CROP_DTYPE", "hist_distance", "DIST_L1",
+           "DIST_INTERSECT", "DIST_CHI2", "CODE_ABS", "CODE_RAW", "CODE_ABS_THRESH", "CODE_RAW_THRESH"]
 
 DESC_DTYPE = np.dtype([("img", "<u8"), ("H", "<i4"), ("W", "<i4"), ("pitch", "<i4"),
                        ("code_pitch", "<i4"), ("codes", "<u8"), ("hist_offset", "<u8")])
@@ -244,6 +245,33 @@ def batch_resize(d_descs, count: int, out_hw=(260, 260), stream=None) -> None:
     rejected descriptors are skipped and reported by device_status() (bit 3)."""
     _abi.call("ldp_batch_resize", ctypes.c_void_p(d_descs.data_ptr()), int(count), int(out_hw[0]),
               int(out_hw[1]), _stream(stream))
+
+
+DIST_L1, DIST_INTERSECT, DIST_CHI2 = _abi.LDP_DIST_L1, _abi.LDP_DIST_INTERSECT, _abi.LDP_DIST_CHI2
+
+
+def hist_distance(q, g, metric: int = DIST_CHI2, out=None, stream=None):
+    """Distances between descriptor rows (e.g. flattened region / window
+    histograms): q (nq, D) and g (ng, D) CUDA int32 tensors holding uint32
+    counts, unit column stride.  Returns (nq, ng): int64 for L1 /
+    intersection, float32 for chi-square."""
+    torch = _torch()
+    for t in (q, g):
+        if not t.is_cuda or t.dim() != 2 or t.stride(1) != 1 or t.dtype not in (torch.int32,):
+            raise ValueError("descriptors must be 2-D int32 CUDA tensors with unit column stride")
+    if q.shape[1] != g.shape[1]:
+        raise ValueError("descriptor lengths differ")
+    nq, D = q.shape
+    ng = g.shape[0]
+    dt = torch.float32 if metric == DIST_CHI2 else torch.int64
+    if out is None:
+        out = torch.empty((nq, ng), dtype=dt, device=q.device)
+    elif out.dtype != dt or tuple(out.shape) != (nq, ng) or out.stride(1) != 1:
+        raise ValueError(f"out must be a {dt} tensor of shape {(nq, ng)} with unit column stride")
+    _abi.call("ldp_hist_distance", ctypes.c_void_p(q.data_ptr()), nq, int(q.stride(0)),
+              ctypes.c_void_p(g.data_ptr()), ng, int(g.stride(0)), D, int(metric),
+              ctypes.c_void_p(out.data_ptr()), int(out.stride(0)), _stream(stream))
+    return out
 
 
 def num_variants() -> int:

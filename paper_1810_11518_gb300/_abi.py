@@ -25,6 +25,9 @@ LDP_CODE_ABS_THRESH = 2  # every i with |m_i| >= the k-th largest |m|
 LDP_CODE_RAW_THRESH = 3  # every i with m_i >= the k-th largest m
 
 
+LDP_DIST_L1, LDP_DIST_INTERSECT, LDP_DIST_CHI2 = 0, 1, 2
+
+
 def plan_code_mode(m: int) -> int:
     return (int(m) & 3) << 2
 
@@ -38,7 +41,7 @@ EXPORTS = [
     "ldp_server_create", "ldp_server_submit", "ldp_server_poll", "ldp_server_stats", "ldp_server_destroy",
     "ldp_window_count", "ldp_window_scratch_bytes", "ldp_window_hist", "lbp_window_hist",
     "ldp_batch_window_scratch_bytes", "ldp_batch_window_hist", "ldp_codes_ex", "ldp_region_hist_ex",
-    "ldp_resize", "ldp_batch_resize",
+    "ldp_resize", "ldp_batch_resize", "ldp_hist_distance",
 ]
 
 
@@ -127,6 +130,7 @@ def load(path: str | None = None):
             "ldp_codes_ex": [vp, i32, i32, i32, i32, i32, vp, i32, vp],
             "ldp_resize": [vp, i32, i32, i32, i32, i32, i32, i32, vp, i32, i32, i32, vp],
             "ldp_batch_resize": [vp, i32, i32, i32, vp],
+            "ldp_hist_distance": [vp, i32, i32, vp, i32, i32, i32, i32, vp, i32, vp],
             "ldp_region_hist_ex": [vp, i32, i32, i32, i32, i32, RegionSpec, vp, vp, i32, vp],
             "ldp_window_scratch_bytes": [i32, i32, i32, WindowSpec, i32],
             "ldp_window_hist": [vp, i32, i32, i32, i32, WindowSpec, vp, vp, i32, vp, u64, vp],

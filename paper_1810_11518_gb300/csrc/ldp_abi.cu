@@ -242,6 +242,19 @@ int ldp_batch_resize(const ldp_crop_desc* d_descs, int count, int OH, int OW, vo
     return LDP_OK;
 }
 
+int ldp_hist_distance(const uint32_t* d_q, int nq, int ldq, const uint32_t* d_g, int ng, int ldg, int D,
+                      int metric, void* d_out, int ldo, void* stream) {
+    if (!d_q || !d_g || !d_out) return fail(LDP_EINVAL, "descriptor or output pointer is NULL");
+    if (nq < 1 || ng < 1 || D < 1) return fail(LDP_EINVAL, "nq, ng and D must be at least 1");
+    if (nq > (1 << 22) || ng > (1 << 30)) return fail(LDP_EINVAL, "nq or ng too large");
+    if (ldq < D || ldg < D || ldo < ng) return fail(LDP_EINVAL, "leading dimension too small");
+    if (metric < LDP_DIST_L1 || metric > LDP_DIST_CHI2) return fail(LDP_EINVAL, "metric must be one of LDP_DIST_*");
+    cudaError_t e = ldp::launch_distance(d_q, nq, ldq, d_g, ng, ldg, D, metric, d_out, ldo,
+                                         static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "distance kernel");
+    return LDP_OK;
+}
+
 int ldp_window_count(int n, int w, int s) {
     if (w < 1 || s < 1 || n < 0) return -1;
     return n <= w ? 1 : (n - w + s - 1) / s + 1;

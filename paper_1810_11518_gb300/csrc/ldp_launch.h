@@ -105,6 +105,10 @@ cudaError_t launch_windows(const ldp_image_desc* d_descs, const ldp_image_desc* 
 cudaError_t launch_resize(const ldp_crop_desc* d_descs, const ldp_crop_desc* one, int count, int OH, int OW,
                           int* status, cudaStream_t s);
 
+// Descriptor distances (ldp_distance.cu), metric LDP_DIST_*.
+cudaError_t launch_distance(const uint32_t* q, int nq, int ldq, const uint32_t* g, int ng, int ldg, int D,
+                            int metric, void* out, int ldo, cudaStream_t s);
+
 cudaError_t read_clear_status(cudaStream_t s, int* out);
 // Device address of the status word on the current device (looked up once per device).
 int* status_word();

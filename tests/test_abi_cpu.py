@@ -179,3 +179,15 @@ def test_resize_arguments_without_gpu(lib):
     assert lib.ldp_batch_resize(None, 1, 26, 26, None) == EINVAL
     assert lib.ldp_batch_resize(fake, 0, 26, 26, None) == EINVAL
     assert lib.ldp_batch_resize(fake, 1, 0, 26, None) == EINVAL
+
+
+def test_distance_arguments_without_gpu(lib):
+    from paper_1810_11518_gb300 import _abi
+
+    EINVAL = _abi.LDP_EINVAL
+    f = ctypes.c_void_p(0x1000)
+    ok = [f, 4, 10, f, 5, 10, 10, _abi.LDP_DIST_CHI2, f, 5, None]
+    for pos, val in ((0, None), (1, 0), (2, 9), (5, 9), (6, 0), (7, 3), (7, -1), (8, None), (9, 4)):
+        args = list(ok)
+        args[pos] = val
+        assert lib.ldp_hist_distance(*args) == EINVAL, (pos, val)
