@@ -76,9 +76,9 @@ def dist_env():
 # profiles/k_batch_ldp_k3_512img_full.md), scaled to a launch by its pixels.
 # Valid only for the kernel sources it was taken on: any change to them
 # reports traffic as null until a new capture is recorded here.
-TRAFFIC_PER_PX = 301.27e6 / (512 * 640 * 490)
+TRAFFIC_PER_PX = 300.757e6 / (512 * 640 * 490)
 TRAFFIC_SOURCES = ("paper_1810_11518_gb300/csrc/ldp_device.cuh", "paper_1810_11518_gb300/csrc/ldp_kernels.cu")
-TRAFFIC_SHA256 = "280a6ea11ab325ab444a25528e5ed73d1c9f78c5f90d79f27f64c8da99fe98db"
+TRAFFIC_SHA256 = "8fd5687da69ee9f174f5f81c041163d871d0c07b49ce7cee1ad08bf8a4f28faa"
 
 
 def measured_traffic(pixels, k, H, W):
@@ -569,8 +569,8 @@ def main():
         extras["distances"] = time_distances(ldp, torch, dev, d_hist, n, hist_len, 5)
         extras["face_pipeline"] = time_face_pipeline(ldp, torch, dev, lay, d_img, k, max(5, a.steps // 10))
         extras["windows"] = [
-            time_windows(ldp, torch, dev, 4096, 260, 260, k, (20, 20), None, max(5, a.steps // 10)),
-            time_windows(ldp, torch, dev, 4096, 490, 640, k, (20, 20), (10, 10), max(5, a.steps // 10)),
+            time_windows(ldp, torch, dev, n, 260, 260, k, (20, 20), None, max(5, a.steps // 10)),
+            time_windows(ldp, torch, dev, n, H, W, k, (20, 20), (10, 10), max(5, a.steps // 10)),
         ]
     if a.large and rank == 0:
         # ---- large images: 64 x 8192^2 (sigma 6), 16x16 regions, k = 1..4 ----
