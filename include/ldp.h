@@ -290,6 +290,40 @@ LDP_API const char *ldp_variant_name(int variant);
 /* Variant used by the single-image entry points (default 0). */
 LDP_API int ldp_set_plain_variant(int variant);
 
+/* ---- host-to-host pipeline: copies and compute overlapped ---- */
+
+/* Extraction of images that live in host memory: the batch is cut into
+ * chunks of consecutive images (at most chunk_images images and chunk_pixels
+ * pixels each); chunk c goes through device buffer c % nbuf -- images copied
+ * in, codes and histograms computed by that buffer's batch plan (k, rs and
+ * flags as ldp_batch_plan_create), results copied back -- on the buffer's
+ * own stream, so copy-in, kernels and copy-out of different chunks overlap.
+ * The pipeline owns nbuf device buffers (grown on first use), plans and
+ * streams.  EINVAL: bad sizes, nbuf outside [1, 8], LDP_PLAN_NO_GRAPH;
+ * ENOMEM on allocation failure. */
+typedef struct ldp_pipeline ldp_pipeline;
+LDP_API int ldp_pipeline_create(ldp_pipeline **out, int chunk_images, uint64_t chunk_pixels, int k,
+                                ldp_region_spec rs, int nbuf, unsigned flags);
+
+/* Runs `count` images: image i at h_img + img_off[i] (H[i] x W[i], row
+ * pitch[i]; offsets non-decreasing), its codes to h_codes + code_off[i] with
+ * code_pitch[i] (h_codes NULL: no codes), its histograms to
+ * h_hist + i * (R*C*nbins).  Host buffers should be pinned; they must stay
+ * valid until `stream` has passed the run: the pipeline starts after work
+ * already queued on `stream`, and `stream` waits for the whole run, so
+ * synchronising it means every result is in place.  The host arrays are read
+ * before the call returns. */
+LDP_API int ldp_pipeline_run(ldp_pipeline *p, int count, const uint8_t *h_img, const int64_t *img_off,
+                             const int *H, const int *W, const int *pitch, uint8_t *h_codes,
+                             const int64_t *code_off, const int *code_pitch, uint32_t *h_hist, void *stream);
+
+/* Tile variant and CTAs per SM of every plan of the pipeline (as
+ * ldp_batch_plan_set_config). */
+LDP_API int ldp_pipeline_set_config(ldp_pipeline *p, int variant, int ctas_per_sm);
+
+/* Waits for the pipeline's work and frees everything it owns.  NULL is a no-op. */
+LDP_API int ldp_pipeline_destroy(ldp_pipeline *p);
+
 /* ---- serving: continuous batching of single-image requests ---- */
 
 /* A request runtime: images submitted one by one from host memory are

@@ -23,7 +23,7 @@ from ._abi import LdpError, RegionSpec, WindowSpec
 __all__ = ["codes", "region_hist", "lbp_codes", "lbp_region_hist", "hist_bins", "bin_of_code",
            "BatchPlan", "BatchLayout", "DESC_DTYPE", "LdpError", "device_status", "num_variants",
            "variant_name", "set_plain_variant", "load", "batch_run_noalloc", "window_count", "window_hist",
-           "lbp_window_hist", "batch_window_hist", "resize", "batch_resize", "CROP_DTYPE", "hist_distance", "DIST_L1",
+           "lbp_window_hist", "batch_window_hist", "resize", "batch_resize", "CROP_DTYPE", "hist_distance", "Pipeline", "DIST_L1",
            "DIST_INTERSECT", "DIST_CHI2", "CODE_ABS", "CODE_RAW", "CODE_ABS_THRESH", "CODE_RAW_THRESH"]
 
 DESC_DTYPE = np.dtype([("img", "<u8"), ("H", "<i4"), ("W", "<i4"), ("pitch", "<i4"),
@@ -272,6 +272,66 @@ def hist_distance(q, g, metric: int = DIST_CHI2, out=None, stream=None):
               ctypes.c_void_p(g.data_ptr()), ng, int(g.stride(0)), D, int(metric),
               ctypes.c_void_p(out.data_ptr()), int(out.stride(0)), _stream(stream))
     return out
+
+
+class Pipeline:
+    """Extraction of images in (pinned) host memory with copies and compute
+    overlapped: chunks of consecutive images rotate over nbuf device buffers,
+    each with its own stream and batch plan (ldp_pipeline_* in include/ldp.h)."""
+
+    def __init__(self, chunk_images: int, chunk_pixels: int, k: int = 3, regions=(7, 6), compact: bool = True,
+                 lbp: bool = False, nbuf: int = 3, code_mode: int = CODE_ABS):
+        self.k = k
+        self.regions = tuple(regions)
+        exact = not lbp and code_mode in (CODE_ABS, CODE_RAW)
+        self.nbins = comb(8, k) if (compact and exact) else 256
+        flags = (_abi.LDP_PLAN_LBP if lbp else 0) | _abi.plan_code_mode(code_mode)
+        h = ctypes.c_void_p()
+        _abi.call("ldp_pipeline_create", ctypes.byref(h), int(chunk_images), int(chunk_pixels), int(k),
+                  RegionSpec(self.regions[0], self.regions[1], int(compact and not lbp)), int(nbuf), flags)
+        self._h = h
+
+    @property
+    def hist_len(self) -> int:
+        return self.regions[0] * self.regions[1] * self.nbins
+
+    def set_config(self, variant: int, ctas_per_sm: int = 0) -> None:
+        _abi.call("ldp_pipeline_set_config", self._h, int(variant), int(ctas_per_sm))
+
+    def run(self, h_img, layout: "BatchLayout", h_hist, h_codes=None, stream=None) -> None:
+        """Queues the extraction of every image of `layout` held in the host
+        buffer h_img (uint8) into h_hist (int32, n x hist_len) and, when given,
+        h_codes (uint8, layout.code_bytes).  Results are in place once
+        `stream` (default: the current stream) has been synchronised."""
+        arrs = [np.ascontiguousarray(layout.img_off, dtype=np.int64),
+                np.ascontiguousarray(layout.Hs, dtype=np.int32), np.ascontiguousarray(layout.Ws, dtype=np.int32),
+                np.ascontiguousarray(layout.pitches, dtype=np.int32),
+                np.ascontiguousarray(layout.code_off, dtype=np.int64),
+                np.ascontiguousarray(layout.code_pitches, dtype=np.int32)]
+        if h_hist.numel() < layout.n * self.hist_len:
+            raise ValueError("h_hist is smaller than n x hist_len")
+        cptr = ctypes.c_void_p(h_codes.data_ptr()) if h_codes is not None else None
+        _abi.call("ldp_pipeline_run", self._h, layout.n, ctypes.c_void_p(h_img.data_ptr()),
+                  *[ctypes.c_void_p(a.ctypes.data) for a in arrs[:4]], cptr,
+                  *[ctypes.c_void_p(a.ctypes.data) for a in arrs[4:]], ctypes.c_void_p(h_hist.data_ptr()),
+                  _stream(stream))
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) and self._h.value:
+            _abi.call("ldp_pipeline_destroy", self._h)
+            self._h = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def num_variants() -> int:

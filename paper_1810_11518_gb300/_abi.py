@@ -41,7 +41,8 @@ EXPORTS = [
     "ldp_server_create", "ldp_server_submit", "ldp_server_poll", "ldp_server_stats", "ldp_server_destroy",
     "ldp_window_count", "ldp_window_scratch_bytes", "ldp_window_hist", "lbp_window_hist",
     "ldp_batch_window_scratch_bytes", "ldp_batch_window_hist", "ldp_codes_ex", "ldp_region_hist_ex",
-    "ldp_resize", "ldp_batch_resize", "ldp_hist_distance",
+    "ldp_resize", "ldp_batch_resize", "ldp_hist_distance", "ldp_pipeline_create", "ldp_pipeline_run",
+    "ldp_pipeline_destroy", "ldp_pipeline_set_config",
 ]
 
 
@@ -131,6 +132,10 @@ def load(path: str | None = None):
             "ldp_resize": [vp, i32, i32, i32, i32, i32, i32, i32, vp, i32, i32, i32, vp],
             "ldp_batch_resize": [vp, i32, i32, i32, vp],
             "ldp_hist_distance": [vp, i32, i32, vp, i32, i32, i32, i32, vp, i32, vp],
+            "ldp_pipeline_create": [ctypes.POINTER(vp), i32, u64, i32, RegionSpec, i32, u32],
+            "ldp_pipeline_run": [vp, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp],
+            "ldp_pipeline_destroy": [vp],
+            "ldp_pipeline_set_config": [vp, i32, i32],
             "ldp_region_hist_ex": [vp, i32, i32, i32, i32, i32, RegionSpec, vp, vp, i32, vp],
             "ldp_window_scratch_bytes": [i32, i32, i32, WindowSpec, i32],
             "ldp_window_hist": [vp, i32, i32, i32, i32, WindowSpec, vp, vp, i32, vp, u64, vp],

@@ -65,6 +65,7 @@ def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -
         (os.path.join(CSRC, "ldp_windows.cu"), os.path.join(BUILD, "ldp_windows.o"), []),
         (os.path.join(CSRC, "ldp_resize.cu"), os.path.join(BUILD, "ldp_resize.o"), []),
         (os.path.join(CSRC, "ldp_distance.cu"), os.path.join(BUILD, "ldp_distance.o"), []),
+        (os.path.join(CSRC, "ldp_pipeline.cu"), os.path.join(BUILD, "ldp_pipeline.o"), []),
     ]
     for vid, rpw, nw, mb, st in variants():
         units.append((os.path.join(CSRC, "ldp_kernels.cu"), os.path.join(BUILD, f"ldp_kernels_v{vid}.o"),

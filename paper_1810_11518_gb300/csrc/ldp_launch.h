@@ -110,6 +110,8 @@ cudaError_t launch_distance(const uint32_t* q, int nq, int ldq, const uint32_t* 
                             int metric, void* out, int ldo, cudaStream_t s);
 
 cudaError_t read_clear_status(cudaStream_t s, int* out);
+// Records msg as the calling thread's ldp_last_error() text; returns code.
+int report_error(int code, const char* msg);
 // Device address of the status word on the current device (looked up once per device).
 int* status_word();
 

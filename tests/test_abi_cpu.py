@@ -191,3 +191,20 @@ def test_distance_arguments_without_gpu(lib):
         args = list(ok)
         args[pos] = val
         assert lib.ldp_hist_distance(*args) == EINVAL, (pos, val)
+
+
+def test_pipeline_arguments_without_gpu(lib):
+    from paper_1810_11518_gb300 import _abi
+
+    EINVAL = _abi.LDP_EINVAL
+    h = ctypes.c_void_p()
+    rs = _abi.RegionSpec(7, 6, 1)
+    assert lib.ldp_pipeline_create(None, 16, 1 << 20, 3, rs, 3, 0) == EINVAL
+    assert lib.ldp_pipeline_create(ctypes.byref(h), 0, 1 << 20, 3, rs, 3, 0) == EINVAL
+    assert lib.ldp_pipeline_create(ctypes.byref(h), 16, 4, 3, rs, 3, 0) == EINVAL
+    assert lib.ldp_pipeline_create(ctypes.byref(h), 16, 1 << 20, 3, rs, 0, 0) == EINVAL
+    assert lib.ldp_pipeline_create(ctypes.byref(h), 16, 1 << 20, 3, rs, 9, 0) == EINVAL
+    assert lib.ldp_pipeline_create(ctypes.byref(h), 16, 1 << 20, 3, rs, 3, _abi.LDP_PLAN_NO_GRAPH) == EINVAL
+    f = ctypes.c_void_p(0x1000)
+    assert lib.ldp_pipeline_run(None, 1, f, f, f, f, f, None, None, None, f, None) == EINVAL
+    assert lib.ldp_pipeline_destroy(None) == 0
