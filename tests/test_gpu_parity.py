@@ -29,7 +29,7 @@ def _hist_np(h):
     return h.cpu().numpy().astype(np.uint32)
 
 
-def test_config1_plain_whole_image(env):
+def test_640x490_plain_whole_image(env):
     """640x490 image from seed 0 (sigma 3), k = 3, 638x488 codes and one
     256-bin whole-image histogram."""
     torch, ldp, oracle, synth = env

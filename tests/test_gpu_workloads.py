@@ -70,7 +70,7 @@ def _compare_all(env, lay, host, d_codes, d_hist, hist_len, k, R, C, compact, mo
         assert np.array_equal(lay.codes(cc, i), c_ref[j]), f"codes of image {i}"
 
 
-def test_config2_4096_faces_ldp_and_lbp(env):
+def test_4096_images_640x490_ldp_and_lbp(env):
     torch, ldp, oracle, synth = env
     n, H, W = 4096, 490, 640
     lay = ldp.BatchLayout.build([H] * n, [W] * n, hist_len=7 * 6 * 56)
@@ -89,7 +89,7 @@ def test_config2_4096_faces_ldp_and_lbp(env):
     _compare_all(env, lay, host, d_codes, d_hist, 256, 3, 1, 1, False, oracle.MODE_LBP)
 
 
-def test_config3_uneven_2048(env):
+def test_2048_uneven_images(env):
     torch, ldp, oracle, synth = env
     n = 2048
     sizes = [synth.sizes(s, 64, 1024) for s in range(n)]
@@ -116,7 +116,7 @@ def large_batch(env):
 
 
 @pytest.mark.parametrize("k", [1, 2, 3, 4])
-def test_config4_8192_squared(env, large_batch, k):
+def test_64_images_8192_squared(env, large_batch, k):
     torch, ldp, oracle, synth = env
     lay, host = large_batch
     nb = ldp.hist_bins(k)
