@@ -7,8 +7,10 @@
 // arithmetic, and
 //     out = (wy0 (wx0 p00 + wx1 p01) + wy1 (wx0 p10 + wx1 p11) + 2^21) >> 22
 // (at most 2048 * 2048 * 255 + 2^21 < 2^32).  A CTA owns kRows output rows of
-// one image: the rows' coordinates are computed once into shared memory,
-// each thread owns output columns (coalesced stores) and their coordinates.
+// one image: the rows' coordinates and source row addresses are computed once
+// into shared memory, each thread owns output columns (coalesced stores) and
+// computes their coordinates once for all kRows rows, in 32-bit arithmetic
+// whenever the numbers fit.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -19,11 +21,35 @@ namespace ldp {
 
 namespace {
 
-constexpr int kRows = 16;
+constexpr int kRows = 32;
 constexpr int kThreads = 256;
 constexpr int kStatusBadCrop = 8;  // device status bit: a crop descriptor was rejected
 
 __device__ __forceinline__ void coord(int i, int n_src, int n_dst, int& i0, int& w1) {
+    // y = num / den with num = (2i + 1) n_src - n_dst, den = 2 n_dst
+    if ((2LL * i + 1) * (long long)n_src < (1LL << 31) && 2LL * n_dst * 2048 < (1LL << 31)) {
+        const int num = (2 * i + 1) * n_src - n_dst, den = 2 * n_dst;
+        if (num <= 0) {
+            i0 = 0;
+            w1 = 0;
+            return;
+        }
+        int q = (int)((unsigned)num / (unsigned)den);
+        const int r = num - q * den;
+        int w = (int)((unsigned)(r * 2048 + den / 2) / (unsigned)den);
+        if (w == 2048) {
+            q += 1;
+            w = 0;
+        }
+        if (q >= n_src - 1) {
+            i0 = n_src - 1;
+            w1 = 0;
+            return;
+        }
+        i0 = q;
+        w1 = w;
+        return;
+    }
     const long long num = (2LL * i + 1) * (long long)n_src - (long long)n_dst;
     const long long den = 2LL * n_dst;
     if (num <= 0) {
@@ -55,7 +81,9 @@ struct ResizeArgs {
 };
 
 __global__ void __launch_bounds__(kThreads) k_resize(ResizeArgs a) {
-    __shared__ int s_y0[kRows], s_y1[kRows], s_wy1[kRows];
+    __shared__ const uint8_t* s_pa[kRows];
+    __shared__ const uint8_t* s_pb[kRows];
+    __shared__ uint32_t s_wy1[kRows];
     const int r0 = blockIdx.x * kRows;
     for (int img = blockIdx.y; img < a.count; img += gridDim.y) {
         const ldp_crop_desc d = a.descs ? a.descs[img] : a.one;
@@ -69,25 +97,28 @@ __global__ void __launch_bounds__(kThreads) k_resize(ResizeArgs a) {
         if (threadIdx.x < kRows && r0 + (int)threadIdx.x < a.OH) {
             int y0, w;
             coord(r0 + threadIdx.x, d.ch, a.OH, y0, w);
-            s_y0[threadIdx.x] = d.cy + y0;
-            s_y1[threadIdx.x] = d.cy + (y0 + 1 < d.ch ? y0 + 1 : y0);
-            s_wy1[threadIdx.x] = w;
+            const int y1 = y0 + 1 < d.ch ? y0 + 1 : y0;
+            s_pa[threadIdx.x] = d.src + (size_t)(d.cy + y0) * (size_t)d.pitch + d.cx;
+            s_pb[threadIdx.x] = d.src + (size_t)(d.cy + y1) * (size_t)d.pitch + d.cx;
+            s_wy1[threadIdx.x] = (uint32_t)w;
         }
         __syncthreads();
         const int nr = min(kRows, a.OH - r0);
+        uint8_t* drow = d.dst + (size_t)r0 * (size_t)d.dst_pitch;
         for (int j = threadIdx.x; j < a.OW; j += blockDim.x) {
             int x0, wx1;
             coord(j, d.cw, a.OW, x0, wx1);
-            const int xa = d.cx + x0, xb = d.cx + (x0 + 1 < d.cw ? x0 + 1 : x0);
+            const int xb = x0 + 1 < d.cw ? x0 + 1 : x0;
             const uint32_t wx0 = 2048u - (uint32_t)wx1;
-            for (int r = 0; r < nr; ++r) {
-                const uint8_t* pa = d.src + (size_t)s_y0[r] * (size_t)d.pitch;
-                const uint8_t* pb = d.src + (size_t)s_y1[r] * (size_t)d.pitch;
-                const uint32_t top = wx0 * __ldg(pa + xa) + (uint32_t)wx1 * __ldg(pa + xb);
-                const uint32_t bot = wx0 * __ldg(pb + xa) + (uint32_t)wx1 * __ldg(pb + xb);
-                const uint32_t wy1 = (uint32_t)s_wy1[r];
+            uint8_t* dp = drow + j;
+            for (int r = 0; r < nr; ++r, dp += d.dst_pitch) {
+                const uint8_t* pa = s_pa[r];
+                const uint8_t* pb = s_pb[r];
+                const uint32_t top = wx0 * __ldg(pa + x0) + (uint32_t)wx1 * __ldg(pa + xb);
+                const uint32_t bot = wx0 * __ldg(pb + x0) + (uint32_t)wx1 * __ldg(pb + xb);
+                const uint32_t wy1 = s_wy1[r];
                 const uint32_t v = (2048u - wy1) * top + wy1 * bot;
-                d.dst[(size_t)(r0 + r) * (size_t)d.dst_pitch + j] = (uint8_t)((v + (1u << 21)) >> 22);
+                *dp = (uint8_t)((v + (1u << 21)) >> 22);
             }
         }
     }

@@ -4,9 +4,12 @@
 // pixels only.  Every window is a union of cells of the grid with cell size
 // (gcd(wh, sh), gcd(ww, sw)), so the work is
 //   k_cell_hist:   one pass over the code map; a CTA owns a row of cells (a
-//                  chunk of it for wide images) and counts its codes in
-//                  shared memory, then stores the cells' histograms (no
-//                  global atomics: every cell belongs to exactly one CTA);
+//                  chunk of it for wide images) -- or, when all of an
+//                  image's cells fit in shared memory, the whole image
+//                  (k_cell_hist_image) -- and counts its codes there, four
+//                  codes per lane and load, then stores the cells'
+//                  histograms (no global atomics: every cell belongs to
+//                  exactly one CTA);
 //   k_window_sum:  each window histogram is the sum of its cells' (skipped
 //                  when stride = size: the cells are the windows).
 // Images come from ldp_image_desc records (batches) or one record passed by
@@ -23,7 +26,7 @@ namespace ldp {
 namespace {
 
 constexpr int kCellThreads = 256;
-constexpr int kCellSmemWords = 12160;  // counters: with the 512-byte table, 48 KB of static shared memory
+constexpr int kCellSmemWords = 12160;  // counters at most: with the 512-byte table, 48 KB of shared memory
 
 struct CellArgs {
     const ldp_image_desc* descs;  // nullptr: the single image `one`
@@ -41,13 +44,27 @@ __device__ __forceinline__ ldp_image_desc desc_of(const CellArgs& a, int i) {
     return a.descs ? a.descs[i] : a.one;
 }
 
+// Cell of column y: y / cw, from a float estimate corrected by one step
+// either way (exact for y < 2^21; image sides are at most 2^20).
+__device__ __forceinline__ int cell_of(int y, int cw, float inv_cw) {
+    int q = (int)((float)y * inv_cw);
+    if (q * cw > y) --q;
+    if ((q + 1) * cw <= y) ++q;
+    return q;
+}
+
 // CTA work item p = (image, cell row) pairs, strided over the grid; the
-// grid's y index picks the chunk of cells along the row.
+// grid's y index picks the chunk of cells along the row.  Warps take the
+// item's rows, lanes four consecutive columns (one 32-bit load of codes when
+// the row is 4-byte aligned), blocks of 128 columns at a time; the four
+// columns' cells are found once per block and reused for every row.
 __global__ void __launch_bounds__(kCellThreads) k_cell_hist(CellArgs a, int count, int ncr_max) {
-    __shared__ uint32_t cnt[kCellSmemWords];
+    extern __shared__ uint32_t cnt[];  // a.chunk * a.nbins counters (sized at launch)
     __shared__ int16_t lut[256];
     for (int c = threadIdx.x; c < 256; c += blockDim.x)
         lut[c] = (a.k >= 1) ? __ldg(&g_bin_table.bin[a.k][c]) : (int16_t)c;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const float inv_cw = 1.0f / (float)a.cw;
     const uint64_t pairs = (uint64_t)count * (uint64_t)ncr_max;
     for (uint64_t p = blockIdx.x; p < pairs; p += gridDim.x) {
         const int img = (int)(p / (uint64_t)ncr_max), i = (int)(p % (uint64_t)ncr_max);
@@ -64,17 +81,95 @@ __global__ void __launch_bounds__(kCellThreads) k_cell_hist(CellArgs a, int coun
         // interior pixels of cell row i, cells j0..j1-1 (code (x, y) at codes[(x-1)*Pc + y-1])
         const int x0 = max(i * a.ch, 1), x1 = min((i + 1) * a.ch, H - 1);
         const int y0 = max(j0 * a.cw, 1), y1 = min(j1 * a.cw, W - 1);
-        for (int y = y0 + threadIdx.x; y < y1; y += blockDim.x) {
-            uint32_t* col = cnt + (y / a.cw - j0) * a.nbins;
-            const uint8_t* cp = d.codes + (size_t)(x0 - 1) * (size_t)d.code_pitch + (y - 1);
-            for (int x = x0; x < x1; ++x, cp += d.code_pitch) {
-                const int b = lut[__ldg(cp)];
-                if (b >= 0) atomicAdd(&col[b], 1u);
+        const bool al = (((uintptr_t)d.codes | (uintptr_t)d.code_pitch) & 3u) == 0;
+        for (int yb = y0; yb < y1; yb += 128) {
+            // this lane's four columns: yq .. yq+3 (code columns yq-1 .. yq+2)
+            const int yq = yb + 4 * lane;
+            int off[4];
+            bool in[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                in[t] = yq + t < y1;
+                off[t] = in[t] ? (cell_of(yq + t, a.cw, inv_cw) - j0) * a.nbins : 0;
+            }
+            const bool vec = al && in[3] && ((yq - 1) & 3) == 0;
+#pragma unroll 4
+            for (int x = x0 + warp; x < x1; x += nwarps) {
+                const uint8_t* cp = d.codes + (size_t)(x - 1) * (size_t)d.code_pitch + (yq - 1);
+                uint32_t w4 = 0;
+                if (vec) {
+                    w4 = __ldg(reinterpret_cast<const unsigned int*>(cp));
+                } else {
+#pragma unroll
+                    for (int t = 0; t < 4; ++t)
+                        if (in[t]) w4 |= (uint32_t)__ldg(cp + t) << (8 * t);
+                }
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const int b = lut[(w4 >> (8 * t)) & 0xFFu];
+                    if (in[t] && b >= 0) atomicAdd(&cnt[off[t] + b], 1u);
+                }
             }
         }
         __syncthreads();
         uint32_t* out = a.direct ? a.hist + d.hist_offset : a.cells + (uint64_t)img * a.cell_stride;
         out += ((size_t)i * (size_t)ncc + (size_t)j0) * (size_t)a.nbins;
+        for (int e = threadIdx.x; e < words; e += blockDim.x) out[e] = cnt[e];
+    }
+}
+
+// Whole-image items, for images whose every cell fits in shared memory (the
+// face-sized crops): one CTA per image, counters zeroed and stored once,
+// warps over rows, lanes over four consecutive columns whose cells are found
+// once for all rows.
+__global__ void __launch_bounds__(kCellThreads) k_cell_hist_image(CellArgs a, int count) {
+    extern __shared__ uint32_t cnt[];  // ncr * ncc * nbins counters of the largest image
+    __shared__ int16_t lut[256];
+    for (int c = threadIdx.x; c < 256; c += blockDim.x)
+        lut[c] = (a.k >= 1) ? __ldg(&g_bin_table.bin[a.k][c]) : (int16_t)c;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const float inv_cw = 1.0f / (float)a.cw, inv_ch = 1.0f / (float)a.ch;
+    for (int img = blockIdx.x; img < count; img += gridDim.x) {
+        const ldp_image_desc d = desc_of(a, img);
+        if (d.codes == nullptr) continue;  // uniform over the CTA
+        const int H = d.H, W = d.W;
+        const int ncc = (W + a.cw - 1) / a.cw;
+        const int words = ((H + a.ch - 1) / a.ch) * ncc * a.nbins;
+        __syncthreads();  // lut ready; the previous image's counters are stored
+        for (int e = threadIdx.x; e < words; e += blockDim.x) cnt[e] = 0;
+        __syncthreads();
+        const bool al = (((uintptr_t)d.codes | (uintptr_t)d.code_pitch) & 3u) == 0;
+        for (int yb = 1; yb < W - 1; yb += 128) {
+            const int yq = yb + 4 * lane;  // columns yq .. yq+3 (code columns yq-1 .. yq+2)
+            int off[4];
+            bool in[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                in[t] = yq + t < W - 1;
+                off[t] = in[t] ? cell_of(yq + t, a.cw, inv_cw) * a.nbins : 0;
+            }
+            const bool vec = al && in[3];  // yq - 1 is a multiple of 4
+#pragma unroll 4
+            for (int x = 1 + warp; x < H - 1; x += nwarps) {
+                const int rbase = cell_of(x, a.ch, inv_ch) * ncc * a.nbins;
+                const uint8_t* cp = d.codes + (size_t)(x - 1) * (size_t)d.code_pitch + (yq - 1);
+                uint32_t w4 = 0;
+                if (vec) {
+                    w4 = __ldg(reinterpret_cast<const unsigned int*>(cp));
+                } else {
+#pragma unroll
+                    for (int t = 0; t < 4; ++t)
+                        if (in[t]) w4 |= (uint32_t)__ldg(cp + t) << (8 * t);
+                }
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const int b = lut[(w4 >> (8 * t)) & 0xFFu];
+                    if (in[t] && b >= 0) atomicAdd(&cnt[rbase + off[t] + b], 1u);
+                }
+            }
+        }
+        __syncthreads();
+        uint32_t* out = a.direct ? a.hist + d.hist_offset : a.cells + (uint64_t)img * a.cell_stride;
         for (int e = threadIdx.x; e < words; e += blockDim.x) out[e] = cnt[e];
     }
 }
@@ -153,15 +248,30 @@ cudaError_t launch_windows(const ldp_image_desc* d_descs, const ldp_image_desc* 
     ca.cw = cw;
     ca.nbins = g.nbins;
     ca.k = g.compact ? g.k : 0;
+    const int ncc_max = (max_W + cw - 1) / cw;
     ca.chunk = kCellSmemWords / g.nbins;
+    if (ca.chunk > ncc_max) ca.chunk = ncc_max;  // shared memory sized to what a row of cells needs
     ca.direct = direct ? 1 : 0;
     ca.hist = hist;
     ca.cells = cells;
     ca.cell_stride = cell_stride;
-    const int ncr = (max_H + ch - 1) / ch, ncc = (max_W + cw - 1) / cw;
-    const uint64_t pairs = (uint64_t)count * (uint64_t)ncr;
-    dim3 grid((unsigned)(pairs < (1u << 20) ? pairs : (1u << 20)), (ncc + ca.chunk - 1) / ca.chunk);
-    k_cell_hist<<<grid, kCellThreads, 0, s>>>(ca, count, ncr);
+    const int ncr = (max_H + ch - 1) / ch;
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const uint64_t image_words = (uint64_t)ncr * (uint64_t)ncc_max * (uint64_t)g.nbins;
+    if (image_words <= (uint64_t)kCellSmemWords) {
+        // every cell of an image fits: one CTA per image
+        const unsigned grid = (unsigned)(count < sms * 16 ? count : sms * 16);
+        k_cell_hist_image<<<grid, kCellThreads, sizeof(uint32_t) * (size_t)image_words, s>>>(ca, count);
+    } else {
+        // CTAs loop over (image, cell row) items: a few waves of the GPU
+        const uint64_t pairs = (uint64_t)count * (uint64_t)ncr;
+        const uint64_t cap = (uint64_t)sms * 32;
+        dim3 grid((unsigned)(pairs < cap ? pairs : cap), (ncc_max + ca.chunk - 1) / ca.chunk);
+        k_cell_hist<<<grid, kCellThreads, sizeof(uint32_t) * (size_t)ca.chunk * (size_t)g.nbins, s>>>(ca, count,
+                                                                                                    ncr);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || direct) return e;
     SumArgs sa{};
