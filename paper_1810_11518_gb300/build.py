@@ -7,6 +7,7 @@ csrc/ldp_launch.h).  Objects go to _build/, the library next to this file.
 from __future__ import annotations
 
 import concurrent.futures as cf
+import fcntl
 import glob
 import os
 import re
@@ -51,10 +52,23 @@ def _compile(args: list[str]) -> tuple[list[str], int, str]:
 
 
 def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -> str:
-    """Compile every CUDA translation unit for sm_103a and link libldp.so."""
+    """Compile every CUDA translation unit for sm_103a and link libldp.so.
+
+    Processes that build at the same time (one per rank, parallel test
+    workers) take turns on a lock file; a process that waited finds the
+    library fresh and returns."""
+    os.makedirs(BUILD, exist_ok=True)
+    with open(os.path.join(BUILD, ".lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        try:
+            return _build_locked(force, verbose, jobs)
+        finally:
+            fcntl.flock(lock, fcntl.LOCK_UN)
+
+
+def _build_locked(force: bool, verbose: bool, jobs: int | None) -> str:
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _sources_mtime():
         return LIB
-    os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
     inc = ["-I", os.path.join(ROOT, "include"), "-I", CSRC]
     units = [
