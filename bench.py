@@ -62,6 +62,7 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="measured seconds per serving rate")
     ap.add_argument("--large", action="store_true", help="also time 64 images of 8192x8192, k = 1..4")
     ap.add_argument("--e2e-chunk", type=int, default=128, help="images per chunk of the end-to-end pipeline")
+    ap.add_argument("--e2e-nbuf", type=int, default=3, help="device buffers / streams of the end-to-end pipeline")
     return ap.parse_args()
 
 
@@ -539,7 +540,7 @@ def main():
     h_codes = torch.empty(lay.code_bytes, dtype=torch.uint8, pin_memory=True)
     h_hist = torch.empty(n * hist_len, dtype=torch.int32, pin_memory=True)
     chunk = max(1, min(a.e2e_chunk, n))
-    pipe = ldp.Pipeline(chunk, chunk * H * W, k=k, regions=(7, 6), nbuf=3)
+    pipe = ldp.Pipeline(chunk, chunk * H * W, k=k, regions=(7, 6), nbuf=a.e2e_nbuf)
     pipe.set_config(variant, cps)
 
     def e2e_step():
@@ -557,7 +558,7 @@ def main():
     ems = max_over_ranks(e0.elapsed_time(e1)) / esteps
     e2e = {"value": round(world * pixels / (ems * 1e-3) / 1e6, 3), "unit": UNIT,
            "h2d_bytes_per_step": int(h_img.numel()), "d2h_bytes_per_step": int(h_codes.numel() + 4 * h_hist.numel()),
-           "ms_per_step": round(ems, 4), "api": f"Pipeline: chunks of {chunk} images over 3 buffers / streams"}
+           "ms_per_step": round(ems, 4), "api": f"Pipeline: chunks of {chunk} images over {a.e2e_nbuf} buffers / streams"}
     pipe.close()
 
     clk = clocks.stop()
