@@ -491,7 +491,7 @@ def main():
         calls = [(ctypes.c_void_p(base_i + int(lay.img_off[i])), H, W, int(lay.pitches[i]), k, rs,
                   ctypes.c_void_p(base_h + 4 * i * hist_len), ctypes.c_void_p(base_c + int(lay.code_off[i])),
                   int(lay.code_pitches[i]), sptr) for i in range(n)]
-        ldp.set_plain_variant(0)
+        ldp.set_plain_variant(-1)  # the library picks the tile variant by image size
         f = lib.ldp_region_hist
 
         def plain_step():
@@ -510,7 +510,8 @@ def main():
         pms = max_over_ranks(e0.elapsed_time(e1)) / psteps
         extras["plain"] = {"value": round(world * pixels / (pms * 1e-3) / 1e6, 3), "unit": UNIT,
                            "ms_per_step": round(pms, 4), "launches_per_step": 2 * n,
-                           "note": "one ldp_region_hist C-ABI call (memset + fused kernel) per image"}
+                           "note": "one ldp_region_hist C-ABI call (memset + fused kernel) per image, "
+                                   "tile variant chosen by image size"}
         extras["batched_over_plain"] = round(pms / ms_step, 3)
 
         # ---- LBP batched on the same images ----

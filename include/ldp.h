@@ -287,7 +287,9 @@ LDP_API int ldp_batch_plan_set_config(ldp_batch_plan *plan, int variant, int cta
 LDP_API int ldp_num_variants(void);
 /* Short description of a variant ("r16w4" ...), static storage. */
 LDP_API const char *ldp_variant_name(int variant);
-/* Variant used by the single-image entry points (default 0). */
+/* Variant used by the single-image entry points; -1 (the default) chooses
+ * by image size: short warp tiles for images of few 64-row tiles (their
+ * latency is that of one tile), 64-row tiles for large images. */
 LDP_API int ldp_set_plain_variant(int variant);
 
 /* ---- host-to-host pipeline: copies and compute overlapped ---- */

@@ -14,7 +14,7 @@
 namespace {
 
 thread_local std::string t_err;
-std::atomic<int> g_plain_variant{0};
+std::atomic<int> g_plain_variant{-1};  // -1: chosen per image size
 
 int fail(int code, const char* msg) {
     t_err = msg;
@@ -53,6 +53,35 @@ int check_regions(int R, int C) {
     return LDP_OK;
 }
 
+// Tile variant of a single-image launch: an image of few 64-row tiles keeps
+// most SMs idle and its latency is that of one tile, so smaller images take
+// shorter warp tiles (more tiles in flight); large images keep 64-row tiles
+// (less flush overhead per pixel).  The shortest non-staged variant of each
+// height is used.
+int plain_variant(int H, int W) {
+    const int fixed = g_plain_variant.load();
+    if (fixed >= 0) return fixed;
+    static int v8 = -2, v16 = -2, sms = 0;
+    if (v8 == -2) {
+        v8 = v16 = 0;
+        for (int v = ldp::num_variants() - 1; v >= 0; --v) {
+            const char* name = ldp::variant_name(v);
+            const int th = ldp::variant_tile_h(v);
+            const bool staged = name[0] && name[strlen(name) - 1] == '1';
+            if (!staged && th == 8) v8 = v;
+            if (!staged && th == 16) v16 = v;
+        }
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            sms = 132;
+    }
+    const long long tiles64 = (long long)((H - 2 + 63) / 64) * (long long)((W - 2 + 127) / 128);
+    if (tiles64 < 2LL * sms) return v8;
+    if (tiles64 < 8LL * sms) return v16;
+    return 0;
+}
+
 int run_plain(int mode, const uint8_t* img, int H, int W, int pitch, int k, int R, int C, int compact,
               uint32_t* hist, uint8_t* codes, int code_pitch, void* stream) {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -66,7 +95,7 @@ int run_plain(int mode, const uint8_t* img, int H, int W, int pitch, int k, int 
         cudaError_t e = cudaMemsetAsync(hist, 0, bytes, s);
         if (e != cudaSuccess) return cuda_fail(e, "zeroing the histogram");
     }
-    cudaError_t e = ldp::launch_plain(mode, k, hist != nullptr, g_plain_variant.load(), jb, hc, s);
+    cudaError_t e = ldp::launch_plain(mode, k, hist != nullptr, plain_variant(H, W), jb, hc, s);
     if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
     return LDP_OK;
 }
@@ -129,7 +158,7 @@ int ldp_num_variants(void) { return ldp::num_variants(); }
 const char* ldp_variant_name(int variant) { return ldp::variant_name(variant); }
 
 int ldp_set_plain_variant(int variant) {
-    if (variant < 0 || variant >= ldp::num_variants()) return fail(LDP_EINVAL, "variant out of range");
+    if (variant < -1 || variant >= ldp::num_variants()) return fail(LDP_EINVAL, "variant out of range");
     g_plain_variant.store(variant);
     return LDP_OK;
 }

@@ -46,6 +46,8 @@ def test_variants_listed(lib):
         assert re.fullmatch(r"r\d+w\d+b\d+t[01]", name)
     assert lib.ldp_variant_name(nv) == b""
     assert lib.ldp_set_plain_variant(nv) == 1
+    assert lib.ldp_set_plain_variant(-2) == 1
+    assert lib.ldp_set_plain_variant(-1) == 0  # by image size (the default)
 
 
 def test_host_helpers(lib):

@@ -149,7 +149,7 @@ def test_pitch_and_unaligned_pointers(env):
             h_ref2, c_ref2 = oracle.extract(img2, k=3, R=2, C=2)
             assert np.array_equal(c.cpu().numpy(), c_ref2) and np.array_equal(_hist_np(h), h_ref2), v
     finally:
-        ldp.set_plain_variant(0)
+        ldp.set_plain_variant(-1)
 
 
 def test_many_small_regions_global_path(env):
@@ -205,4 +205,4 @@ def test_all_variants(env):
             assert np.array_equal(c.cpu().numpy(), c_ref), ldp.variant_name(v)
             assert np.array_equal(_hist_np(h), h_ref), ldp.variant_name(v)
     finally:
-        ldp.set_plain_variant(0)
+        ldp.set_plain_variant(-1)
