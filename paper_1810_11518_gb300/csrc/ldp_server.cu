@@ -93,9 +93,10 @@ struct Request {
     int dpitch = 0, dcpitch = 0;
 };
 
-struct Slot {  // one stream with its own plan and staging buffers
+struct Slot {  // one stream with its own plans and staging buffers
     cudaStream_t stream = nullptr;
-    ldp_batch_plan* plan = nullptr;
+    ldp_batch_plan* plan = nullptr;        // the configured tile variant
+    ldp_batch_plan* plan_short = nullptr;  // short warp tiles, for batches of few 64-row tiles
     ldp_image_desc* h_desc = nullptr;  // pinned
     int* h_count = nullptr;            // pinned
     ldp_image_desc* d_desc = nullptr;
@@ -112,6 +113,7 @@ struct Slot {  // one stream with its own plan and staging buffers
 struct ldp_server {
     ldp_server_config cfg{};
     int hist_len = 0;
+    int num_sms = 1;
     uint8_t* d_arena = nullptr;
     Arena* arena = nullptr;
     std::vector<Slot> slots;
@@ -166,7 +168,13 @@ bool launch_batch(ldp_server* s, int si) {
         set_error(s, std::string("server H2D: ") + cudaGetErrorString(e));
         return false;
     }
-    if (ldp_batch_run(sl.plan, sl.d_desc, sl.d_count, s->hist_len ? sl.d_hist : nullptr, sl.stream) != LDP_OK) {
+    // a batch of few 64-row tiles leaves most SMs idle and its latency is that
+    // of one tile: such batches run with short warp tiles (more tiles in flight)
+    long long tiles64 = 0;
+    for (int i = 0; i < n; ++i)
+        tiles64 += (long long)((sl.reqs[i].H - 2 + 63) / 64) * (long long)((sl.reqs[i].W - 2 + 127) / 128);
+    ldp_batch_plan* plan = (sl.plan_short && tiles64 < 2LL * s->num_sms) ? sl.plan_short : sl.plan;
+    if (ldp_batch_run(plan, sl.d_desc, sl.d_count, s->hist_len ? sl.d_hist : nullptr, sl.stream) != LDP_OK) {
         set_error(s, std::string("server batch run: ") + ldp_last_error());
         return false;
     }
@@ -278,6 +286,7 @@ void completer_main(ldp_server* s) {
 void destroy_resources(ldp_server* s) {
     for (Slot& sl : s->slots) {
         if (sl.plan) ldp_batch_plan_destroy(sl.plan);
+        if (sl.plan_short) ldp_batch_plan_destroy(sl.plan_short);
         if (sl.stream) cudaStreamDestroy(sl.stream);
         if (sl.h_desc) cudaFreeHost(sl.h_desc);
         if (sl.h_count) cudaFreeHost(sl.h_count);
@@ -317,6 +326,10 @@ int ldp_server_create(ldp_server** out, const ldp_server_config* cfg) {
         return ldp::report_error(LDP_ENOMEM, "device arena allocation failed");
     }
     s->arena = new Arena(cfg->arena_bytes);
+    {
+        int dev = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    }
     s->slots.resize(cfg->streams);
     const uint64_t max_pixels = cfg->arena_bytes;  // pixels in flight never exceed arena bytes
     for (Slot& sl : s->slots) {
@@ -335,6 +348,18 @@ int ldp_server_create(ldp_server** out, const ldp_server_config* cfg) {
                 return LDP_ENOMEM;
             }
             if (cfg->variant >= 0) ldp_batch_plan_set_config(sl.plan, cfg->variant, cfg->ctas_per_sm);
+            // short tiles: the first non-staged variant of 8-row tiles, unless a variant was fixed
+            int vshort = -1;
+            for (int v = 0; v < ldp::num_variants() && cfg->variant < 0; ++v) {
+                const char* name = ldp::variant_name(v);
+                if (ldp::variant_tile_h(v) == 8 && name[0] && name[strlen(name) - 1] == '0') {
+                    vshort = v;
+                    break;
+                }
+            }
+            if (vshort >= 0 &&
+                ldp_batch_plan_create(&sl.plan_short, cfg->max_batch, max_pixels, cfg->k, cfg->rs, 0) == LDP_OK)
+                ldp_batch_plan_set_config(sl.plan_short, vshort, cfg->ctas_per_sm);
         }
     }
     if (e != cudaSuccess) {
