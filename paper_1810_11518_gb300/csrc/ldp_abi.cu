@@ -56,29 +56,40 @@ int check_regions(int R, int C) {
 // Tile variant of a single-image launch: an image of few 64-row tiles keeps
 // most SMs idle and its latency is that of one tile, so smaller images take
 // shorter warp tiles (more tiles in flight); large images keep 64-row tiles
-// (less flush overhead per pixel).  The shortest non-staged variant of each
+// (less flush overhead per pixel).  The first non-staged variant of each
 // height is used.
-int plain_variant(int H, int W) {
-    const int fixed = g_plain_variant.load();
-    if (fixed >= 0) return fixed;
-    static int v8 = -2, v16 = -2, sms = 0;
-    if (v8 == -2) {
-        v8 = v16 = 0;
-        for (int v = ldp::num_variants() - 1; v >= 0; --v) {
+struct PlainChoice {
+    int v8 = 0, v16 = 0, sms = 132;
+};
+
+// the short-tile variants and the SM count, found once (thread-safe static)
+const PlainChoice& plain_choice() {
+    static const PlainChoice c = [] {
+        PlainChoice r;
+        bool f8 = false, f16 = false;
+        for (int v = 0; v < ldp::num_variants(); ++v) {
             const char* name = ldp::variant_name(v);
             const int th = ldp::variant_tile_h(v);
             const bool staged = name[0] && name[strlen(name) - 1] == '1';
-            if (!staged && th == 8) v8 = v;
-            if (!staged && th == 16) v16 = v;
+            if (!staged && th == 8 && !f8) r.v8 = v, f8 = true;
+            if (!staged && th == 16 && !f16) r.v16 = v, f16 = true;
         }
-        int dev = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess ||
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-            sms = 132;
-    }
+        int dev = 0, sms = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0)
+            r.sms = sms;
+        return r;
+    }();
+    return c;
+}
+
+int plain_variant(int H, int W) {
+    const int fixed = g_plain_variant.load();
+    if (fixed >= 0) return fixed;
+    const PlainChoice& c = plain_choice();
     const long long tiles64 = (long long)((H - 2 + 63) / 64) * (long long)((W - 2 + 127) / 128);
-    if (tiles64 < 2LL * sms) return v8;
-    if (tiles64 < 8LL * sms) return v16;
+    if (tiles64 < 2LL * c.sms) return c.v8;
+    if (tiles64 < 8LL * c.sms) return c.v16;
     return 0;
 }
 
