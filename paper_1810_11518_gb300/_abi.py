@@ -95,7 +95,7 @@ def load(path: str | None = None):
     with _lock:
         if _lib is not None:
             return _lib
-        path = path or LIB_PATH
+        path = path or os.environ.get("LDP_LIBRARY") or LIB_PATH
         if not os.path.exists(path):
             raise ImportError(f"{path} is missing: build it with `python -m paper_1810_11518_gb300.build` "
                               "(nvcc, sm_103a); there is no fallback path")

@@ -19,6 +19,9 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libldp.so")
+# checked build (-DLDP_CHECKED): every tile-loop index tested against its buffer
+BUILD_CHECKED = os.path.join(HERE, "_build_checked")
+LIB_CHECKED = os.path.join(HERE, "libldp_checked.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fvisibility=hidden", "-Xptxas", "-warn-spills"]
 
@@ -51,48 +54,52 @@ def _compile(args: list[str]) -> tuple[list[str], int, str]:
     return args, p.returncode, p.stdout + p.stderr
 
 
-def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -> str:
-    """Compile every CUDA translation unit for sm_103a and link libldp.so.
+def build(force: bool = False, verbose: bool = False, jobs: int | None = None, checked: bool = False) -> str:
+    """Compile every CUDA translation unit for sm_103a and link libldp.so
+    (checked=True: libldp_checked.so with -DLDP_CHECKED, in its own folder).
 
     Processes that build at the same time (one per rank, parallel test
     workers) take turns on a lock file; a process that waited finds the
     library fresh and returns."""
-    os.makedirs(BUILD, exist_ok=True)
-    with open(os.path.join(BUILD, ".lock"), "w") as lock:
+    bdir = BUILD_CHECKED if checked else BUILD
+    os.makedirs(bdir, exist_ok=True)
+    with open(os.path.join(bdir, ".lock"), "w") as lock:
         fcntl.flock(lock, fcntl.LOCK_EX)
         try:
-            return _build_locked(force, verbose, jobs)
+            return _build_locked(force, verbose, jobs, checked)
         finally:
             fcntl.flock(lock, fcntl.LOCK_UN)
 
 
-def _build_locked(force: bool, verbose: bool, jobs: int | None) -> str:
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _sources_mtime():
-        return LIB
+def _build_locked(force: bool, verbose: bool, jobs: int | None, checked: bool) -> str:
+    lib, bdir = (LIB_CHECKED, BUILD_CHECKED) if checked else (LIB, BUILD)
+    extra = ["-DLDP_CHECKED"] if checked else []
+    if not force and os.path.exists(lib) and os.path.getmtime(lib) >= _sources_mtime():
+        return lib
     cc = nvcc()
     inc = ["-I", os.path.join(ROOT, "include"), "-I", CSRC]
     units = [
-        (os.path.join(CSRC, "ldp_common.cu"), os.path.join(BUILD, "ldp_common.o"), []),
-        (os.path.join(CSRC, "ldp_abi.cu"), os.path.join(BUILD, "ldp_abi.o"), []),
-        (os.path.join(CSRC, "ldp_noalloc.cu"), os.path.join(BUILD, "ldp_noalloc.o"), []),
-        (os.path.join(CSRC, "ldp_server.cu"), os.path.join(BUILD, "ldp_server.o"), []),
-        (os.path.join(CSRC, "ldp_windows.cu"), os.path.join(BUILD, "ldp_windows.o"), []),
-        (os.path.join(CSRC, "ldp_resize.cu"), os.path.join(BUILD, "ldp_resize.o"), []),
-        (os.path.join(CSRC, "ldp_distance.cu"), os.path.join(BUILD, "ldp_distance.o"), []),
-        (os.path.join(CSRC, "ldp_pipeline.cu"), os.path.join(BUILD, "ldp_pipeline.o"), []),
+        (os.path.join(CSRC, "ldp_common.cu"), os.path.join(bdir, "ldp_common.o"), []),
+        (os.path.join(CSRC, "ldp_abi.cu"), os.path.join(bdir, "ldp_abi.o"), []),
+        (os.path.join(CSRC, "ldp_noalloc.cu"), os.path.join(bdir, "ldp_noalloc.o"), []),
+        (os.path.join(CSRC, "ldp_server.cu"), os.path.join(bdir, "ldp_server.o"), []),
+        (os.path.join(CSRC, "ldp_windows.cu"), os.path.join(bdir, "ldp_windows.o"), []),
+        (os.path.join(CSRC, "ldp_resize.cu"), os.path.join(bdir, "ldp_resize.o"), []),
+        (os.path.join(CSRC, "ldp_distance.cu"), os.path.join(bdir, "ldp_distance.o"), []),
+        (os.path.join(CSRC, "ldp_pipeline.cu"), os.path.join(bdir, "ldp_pipeline.o"), []),
     ]
     for vid, rpw, nw, mb, st in variants():
-        units.append((os.path.join(CSRC, "ldp_kernels.cu"), os.path.join(BUILD, f"ldp_kernels_v{vid}.o"),
+        units.append((os.path.join(CSRC, "ldp_kernels.cu"), os.path.join(bdir, f"ldp_kernels_v{vid}.o"),
                       [f"-DLDP_VAR_ID={vid}", f"-DLDP_VAR_RPW={rpw}", f"-DLDP_VAR_NW={nw}", f"-DLDP_VAR_MB={mb}",
                        f"-DLDP_VAR_ST={st}"]))
     # the kernels of the other Eq. 2-3 readings (kernel modes 2..4, one unit
     # each), in the tile shape of variant 0
     v0 = variants()[0]
     for cm in (2, 3, 4):
-        units.append((os.path.join(CSRC, "ldp_kernels.cu"), os.path.join(BUILD, f"ldp_kernels_vcm{cm}.o"),
+        units.append((os.path.join(CSRC, "ldp_kernels.cu"), os.path.join(bdir, f"ldp_kernels_vcm{cm}.o"),
                       [f"-DLDP_VAR_ID=cm{cm}", f"-DLDP_VAR_RPW={v0[1]}", f"-DLDP_VAR_NW={v0[2]}",
                        f"-DLDP_VAR_MB={v0[3]}", f"-DLDP_VAR_ST={v0[4]}", f"-DLDP_CODE_MODES={cm}"]))
-    cmds = [[cc] + ARCH + FLAGS + inc + defs + ["-c", src, "-o", obj] for src, obj, defs in units]
+    cmds = [[cc] + ARCH + FLAGS + extra + inc + defs + ["-c", src, "-o", obj] for src, obj, defs in units]
     jobs = jobs or max(1, min(len(cmds), os.cpu_count() or 1))
     with cf.ThreadPoolExecutor(jobs) as ex:
         results = list(ex.map(_compile, cmds))
@@ -101,13 +108,13 @@ def _build_locked(force: bool, verbose: bool, jobs: int | None) -> str:
             raise RuntimeError("nvcc failed:\n" + " ".join(args) + "\n" + out)
         if verbose and out.strip():
             print(out)
-    tmp = LIB + f".{os.getpid()}.tmp"
+    tmp = lib + f".{os.getpid()}.tmp"
     link = [cc] + ARCH + ["-shared", "-o", tmp] + [obj for _, obj, _ in units]
     p = subprocess.run(link, capture_output=True, text=True)
     if p.returncode != 0:
         raise RuntimeError("link failed:\n" + " ".join(link) + "\n" + p.stdout + p.stderr)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -95,6 +95,7 @@ int plain_variant(int H, int W) {
 
 int run_plain(int mode, const uint8_t* img, int H, int W, int pitch, int k, int R, int C, int compact,
               uint32_t* hist, uint8_t* codes, int code_pitch, void* stream) {
+    ldp::Range range("ldp.single_image");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     ldp::JobArgs jb{img, H, W, pitch, codes, code_pitch, hist, ldp::status_word()};
     ldp::HistArgs hc{R, C, 256, 0};
@@ -265,6 +266,7 @@ int ldp_resize(const uint8_t* d_src, int H, int W, int pitch, int cy, int cx, in
     if (dst_pitch < OW) return fail(LDP_EINVAL, "dst_pitch < OW");
     int* status = ldp::status_word();
     if (!status) return fail(LDP_ECUDA, "device status word not found");
+    ldp::Range range("ldp.resize");
     ldp_crop_desc one{d_src, d_dst, H, W, pitch, cy, cx, ch, cw, dst_pitch};
     cudaError_t e = ldp::launch_resize(nullptr, &one, 1, OH, OW, status, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "resize kernel");
@@ -277,6 +279,7 @@ int ldp_batch_resize(const ldp_crop_desc* d_descs, int count, int OH, int OW, vo
     if (OH < 1 || OW < 1 || OH > (1 << 16) || OW > (1 << 16)) return fail(LDP_EINVAL, "output size out of range");
     int* status = ldp::status_word();
     if (!status) return fail(LDP_ECUDA, "device status word not found");
+    ldp::Range range("ldp.batch_resize");
     cudaError_t e = ldp::launch_resize(d_descs, nullptr, count, OH, OW, status, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "resize kernel");
     return LDP_OK;
@@ -289,6 +292,7 @@ int ldp_hist_distance(const uint32_t* d_q, int nq, int ldq, const uint32_t* d_g,
     if (nq > (1 << 22) || ng > (1 << 30)) return fail(LDP_EINVAL, "nq or ng too large");
     if (ldq < D || ldg < D || ldo < ng) return fail(LDP_EINVAL, "leading dimension too small");
     if (metric < LDP_DIST_L1 || metric > LDP_DIST_CHI2) return fail(LDP_EINVAL, "metric must be one of LDP_DIST_*");
+    ldp::Range range("ldp.hist_distance");
     cudaError_t e = ldp::launch_distance(d_q, nq, ldq, d_g, ng, ldg, D, metric, d_out, ldo,
                                          static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "distance kernel");
@@ -328,6 +332,7 @@ uint64_t window_scratch(int H, int W, int k, const ldp_window_spec& ws, bool cod
 int run_windows(int mode, const uint8_t* d_img, int H, int W, int pitch, int k, const ldp_window_spec& ws,
                 uint32_t* d_hist, uint8_t* d_codes, int code_pitch, void* d_scratch, uint64_t scratch_bytes,
                 void* stream) {
+    ldp::Range range("ldp.window_hist");
     int rc;
     if ((rc = check_image(d_img, H, W, pitch))) return rc;
     if ((rc = check_codes(d_codes, W, code_pitch, false))) return rc;
@@ -397,6 +402,7 @@ int ldp_batch_window_hist(const ldp_image_desc* d_descs, int count, int max_H, i
     if (k < 0 || k > 7) return fail(LDP_EINVAL, "k must be in [0,7]");
     if ((rc = check_windows(ws, k))) return rc;
     if (!d_hist) return fail(LDP_EINVAL, "histogram pointer is NULL");
+    ldp::Range range("ldp.batch_window_hist");
     const ldp::WindowGeom g = window_geom(ws, k);
     const uint64_t words = ldp::window_direct(g) ? 0 : ldp::window_cell_words(max_H, max_W, g);
     if (words && (!d_scratch || scratch_bytes < (uint64_t)count * words * sizeof(uint32_t)))
@@ -470,6 +476,7 @@ int ldp_batch_plan_set_config(ldp_batch_plan* plan, int variant, int ctas_per_sm
 
 static int batch_run(ldp_batch_plan* plan, int mode, const ldp_image_desc* d_descs, const int* d_count,
                      uint32_t* d_hist, void* stream) {
+    ldp::Range range("ldp.batch_run");
     if (!plan) return fail(LDP_EINVAL, "plan is NULL");
     if ((plan->mode == 1) != (mode == 1))
         return fail(LDP_EINVAL, "plan was created for the other descriptor (LDP vs LBP)");

@@ -340,6 +340,22 @@ constexpr int kWarpSlots = 6;  // region slots a warp tile may touch and still c
 constexpr int kStageRows = 8, kStages = 3, kRowBytes = 144;
 constexpr int kSpinLimit = 1 << 22;  // bounded mbarrier waits
 constexpr int kStatusWaitTimeout = 4;  // device status bit: a bounded wait gave up
+constexpr int kStatusBounds = 16;      // checked builds: an index outside its buffer was skipped
+
+// Checked builds (-DLDP_CHECKED) test every shared- and global-memory index
+// of the tile loop against its buffer; a violation sets kStatusBounds in the
+// device status word and the access is skipped (nothing traps).  In normal
+// builds the test is compiled away.
+__device__ __forceinline__ bool index_ok(bool ok, int* status) {
+#ifdef LDP_CHECKED
+    if (!ok) atomicOr(status, kStatusBounds);
+    return ok;
+#else
+    (void)status;
+    (void)ok;
+    return true;
+#endif
+}
 
 struct WarpRing {
     alignas(128) uint8_t row[kStages][kStageRows][kRowBytes];
@@ -462,10 +478,10 @@ __device__ __forceinline__ void warp_tile(const Job& jb, const HistCfg& hc, int 
 
     // codes of output row u (byte t of `packed` = column v+t) -> code map and histogram
     auto emit = [&](int u, uint32_t packed) {
-        if (jb.codes) {
+        if (jb.codes && index_ok(u >= 0 && u < H - 2, status)) {
             uint8_t* cp = jb.codes + (size_t)u * (size_t)jb.Pc + v;
             if (fast_st) {
-                *reinterpret_cast<uint32_t*>(cp) = packed;
+                if (index_ok(v + 3 < W - 2, status)) *reinterpret_cast<uint32_t*>(cp) = packed;
             } else {
 #pragma unroll
                 for (int t = 0; t < 4; ++t)
@@ -488,20 +504,25 @@ __device__ __forceinline__ void warp_tile(const Job& jb, const HistCfg& hc, int 
                         const uint32_t code = prmt(packed, 0u, 0x4440u | (uint32_t)t);
                         uint32_t addr;
                         asm("mad.lo.u32 %0, %1, 4, %2;" : "=r"(addr) : "r"(code), "r"(sbase[t]));
-                        asm volatile("red.shared.add.u32 [%0], 1;" ::"r"(addr) : "memory");
+                        if (index_ok(addr - wh_addr < 4u * kWarpSlots * 256u, status))
+                            asm volatile("red.shared.add.u32 [%0], 1;" ::"r"(addr) : "memory");
                     }
             } else if (use_smem) {
                 // LBP: neighbouring lanes often share a code (flat areas give
                 // 255); the compiler's shared atomicAdd is faster there
 #pragma unroll
-                for (int t = 0; t < 4; ++t)
-                    if (valid[t]) atomicAdd(&wh[rowb + colb[t] + (int)((packed >> (8 * t)) & 0xFFu)], 1u);
+                for (int t = 0; t < 4; ++t) {
+                    const int idx = rowb + colb[t] + (int)((packed >> (8 * t)) & 0xFFu);
+                    if (valid[t] && index_ok(idx < kWarpSlots * 256, status)) atomicAdd(&wh[idx], 1u);
+                }
             } else {
 #pragma unroll
                 for (int t = 0; t < 4; ++t)
                     if (valid[t]) {
                         const int code = (int)((packed >> (8 * t)) & 0xFFu);
-                        atomicAdd(&jb.hist[(size_t)(rowb + colb[t]) * hc.nbins + bin_of(code, hc, K)], 1u);
+                        const int bin = bin_of(code, hc, K);
+                        if (index_ok(rowb + colb[t] < hc.R * hc.C && bin >= 0 && bin < hc.nbins, status))
+                            atomicAdd(&jb.hist[(size_t)(rowb + colb[t]) * hc.nbins + bin], 1u);
                     }
             }
         }
@@ -616,7 +637,7 @@ __device__ __forceinline__ void warp_tile(const Job& jb, const HistCfg& hc, int 
         unpack(load_raw(rp + P, v, W, fast_ld), r1);
         auto step = [&](const Row& A, const Row& B, Row& C, int u) {
             unpack(nx, C);
-            if (u + 1 < ue) nx = load_raw(pf, v, W, fast_ld);
+            if (u + 1 < ue && index_ok(u + 3 < H, status)) nx = load_raw(pf, v, W, fast_ld);
             pf += P;
             emit(u, codes_of_row(A, B, C));
         };
@@ -655,7 +676,8 @@ __device__ __forceinline__ void warp_tile(const Job& jb, const HistCfg& hc, int 
                         const uint32_t c = hs[code];
                         if (c) {
                             const int bin = (exact_k(MODE) && hc.compact) ? lane + 32 * m : code;
-                            atomicAdd(&jb.hist[hbase + bin], c);
+                            if (index_ok(hbase + bin < hc.R * hc.C * hc.nbins, status))
+                                atomicAdd(&jb.hist[hbase + bin], c);
                             hs[code] = 0;
                         }
                     }

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cstdint>
 
@@ -10,6 +11,15 @@
 #include "ldp_modes.h"
 
 namespace ldp {
+
+// NVTX range around a host-side call (a named span in profiler timelines; a
+// no-op unless a tool is attached).
+struct Range {
+    explicit Range(const char* name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range&) = delete;
+    Range& operator=(const Range&) = delete;
+};
 
 struct JobArgs {
     const uint8_t* img;

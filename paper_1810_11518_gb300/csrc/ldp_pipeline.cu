@@ -160,6 +160,7 @@ int ldp_pipeline_run(ldp_pipeline* p, int count, const uint8_t* h_img, const int
             if (i && code_off[i] < code_off[i - 1]) return pfail(LDP_EINVAL, "code offsets must not decrease");
         }
     }
+    ldp::Range range("ldp.pipeline_run");
     cudaStream_t cs = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaEventRecord(p->start, cs);
     if (e != cudaSuccess) return pcuda(e, "recording the start event");

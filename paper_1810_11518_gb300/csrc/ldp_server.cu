@@ -138,6 +138,7 @@ void set_error(ldp_server* s, const std::string& msg) {
 
 // Launches one batch on slot `si` from the admitted requests in s->slots[si].reqs.
 bool launch_batch(ldp_server* s, int si) {
+    ldp::Range range("ldp.server.batch");
     Slot& sl = s->slots[si];
     cudaError_t e = cudaSuccess;
     const int n = (int)sl.reqs.size();
