@@ -359,17 +359,40 @@ def time_distances(ldp, torch, dev, d_hist, n, hist_len, steps):
 
 
 def run_reference(a):
+    """The reference arm: the CPU oracle as it stands, on the host cores, on a
+    bounded sample of the workload per step.  The sample is sized so the
+    whole --steps/--warmup run takes about two minutes of oracle time."""
+    import oracle
+    import synth
+
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    n = max(1, min(a.cpu_sample, a.images)) // 4 or 1
+    H, W, k = a.height, a.width, a.k
+    thr = max(1, os.cpu_count() or 1)
+
+    def make(n):
+        imgs = synth.batch(list(range(n)), H, W, 3.0, threads=thr)
+        return imgs.reshape(-1), np.arange(n, dtype=np.int64) * (H * W)
+
+    def extract(flat, offs):
+        n = len(offs)
+        t0 = time.perf_counter()
+        oracle.extract_batch(flat, offs, [H] * n, [W] * n, [W] * n, k=k, R=7, C=6, compact=True, threads=thr,
+                             want_codes=True)
+        return time.perf_counter() - t0
+
+    cal = max(thr, 8)
+    t_img = extract(*make(cal)) / cal
+    budget = 120.0 / max(1, a.steps + a.warmup)
+    n = int(budget / max(t_img, 1e-6)) // thr * thr
+    n = max(thr, min(n, max(thr, min(a.cpu_sample, a.images) // 4)))
+    flat, offs = make(n)
     for _ in range(max(a.warmup, 0)):
-        cpu_oracle_sample(n, a.height, a.width, a.k)
-    vals, total = [], 0.0
+        extract(flat, offs)
+    total = 0.0
     for _ in range(a.steps):
-        v, dt, thr = cpu_oracle_sample(n, a.height, a.width, a.k)
-        vals.append(v)
-        total += dt
+        total += extract(flat, offs)
     value = n * a.height * a.width * a.steps / total / 1e6
     line = {
         "impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": a.gpus,
