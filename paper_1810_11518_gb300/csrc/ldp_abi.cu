@@ -1,9 +1,11 @@
 // C-ABI of libldp (declared in include/ldp.h): argument validation, error
-// reporting, single-image launches, batch plans with CUDA-graph replay.
+// reporting, single-image launches (codes and region histograms in every code
+// mode), batch plans with CUDA-graph replay.  The entry points of sliding
+// windows, crop-and-resize and distances sit beside their kernels
+// (ldp_windows.cu, ldp_resize.cu, ldp_distance.cu).
 #include <cuda_runtime.h>
 
 #include <atomic>
-#include <cstdio>
 #include <cstring>
 #include <new>
 #include <string>
@@ -16,40 +18,10 @@ namespace {
 thread_local std::string t_err;
 std::atomic<int> g_plain_variant{-1};  // -1: chosen per image size
 
-int fail(int code, const char* msg) {
-    t_err = msg;
-    return code;
-}
-
-int cuda_fail(cudaError_t e, const char* where) {
-    t_err = std::string(where) + ": " + cudaGetErrorName(e) + ": " + cudaGetErrorString(e);
-    return LDP_ECUDA;
-}
-
-int binom8(int r) {
-    if (r < 0 || r > 8) return -1;
-    int c = 1;
-    for (int i = 1; i <= r; ++i) c = c * (8 - r + i) / i;
-    return c;
-}
-
-int check_image(const void* img, int H, int W, int pitch) {
-    if (!img) return fail(LDP_EINVAL, "image pointer is NULL");
-    if (H < 3 || W < 3) return fail(LDP_EINVAL, "image must be at least 3x3");
-    if (H > (1 << 20) || W > (1 << 20)) return fail(LDP_EINVAL, "image side larger than 1<<20");
-    if (pitch < W) return fail(LDP_EINVAL, "pitch < W");
-    return LDP_OK;
-}
-
-int check_codes(const void* codes, int W, int code_pitch, bool required) {
-    if (!codes) return required ? fail(LDP_EINVAL, "codes pointer is NULL") : LDP_OK;
-    if (code_pitch < W - 2) return fail(LDP_EINVAL, "code_pitch < W-2");
-    return LDP_OK;
-}
-
 int check_regions(int R, int C) {
-    if (R < 1 || C < 1) return fail(LDP_EINVAL, "region grid must be at least 1x1");
-    if ((int64_t)R * (int64_t)C > (1 << 22)) return fail(LDP_EINVAL, "region grid larger than 1<<22 regions");
+    if (R < 1 || C < 1) return ldp::report_error(LDP_EINVAL, "region grid must be at least 1x1");
+    if ((int64_t)R * (int64_t)C > (1 << 22))
+        return ldp::report_error(LDP_EINVAL, "region grid larger than 1<<22 regions");
     return LDP_OK;
 }
 
@@ -93,31 +65,71 @@ int plain_variant(int H, int W) {
     return 0;
 }
 
+}  // namespace
+
+namespace ldp {
+
+int report_error(int code, const char* msg) {
+    t_err = msg;
+    return code;
+}
+
+int report_cuda(cudaError_t e, const char* where) {
+    t_err = std::string(where) + ": " + cudaGetErrorName(e) + ": " + cudaGetErrorString(e);
+    return LDP_ECUDA;
+}
+
+int binom8(int r) {
+    if (r < 0 || r > 8) return -1;
+    int c = 1;
+    for (int i = 1; i <= r; ++i) c = c * (8 - r + i) / i;
+    return c;
+}
+
+int check_image(const void* img, int H, int W, int pitch) {
+    if (!img) return report_error(LDP_EINVAL, "image pointer is NULL");
+    if (H < 3 || W < 3) return report_error(LDP_EINVAL, "image must be at least 3x3");
+    if (H > (1 << 20) || W > (1 << 20)) return report_error(LDP_EINVAL, "image side larger than 1<<20");
+    if (pitch < W) return report_error(LDP_EINVAL, "pitch < W");
+    return LDP_OK;
+}
+
+int check_codes(const void* codes, int W, int code_pitch, bool required) {
+    if (!codes) return required ? report_error(LDP_EINVAL, "codes pointer is NULL") : LDP_OK;
+    if (code_pitch < W - 2) return report_error(LDP_EINVAL, "code_pitch < W-2");
+    return LDP_OK;
+}
+
 int run_plain(int mode, const uint8_t* img, int H, int W, int pitch, int k, int R, int C, int compact,
               uint32_t* hist, uint8_t* codes, int code_pitch, void* stream) {
-    ldp::Range range("ldp.single_image");
+    Range range("ldp.single_image");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    ldp::JobArgs jb{img, H, W, pitch, codes, code_pitch, hist, ldp::status_word()};
-    ldp::HistArgs hc{R, C, 256, 0};
+    JobArgs jb{img, H, W, pitch, codes, code_pitch, hist, status_word()};
+    HistArgs hc{R, C, 256, 0};
     if (hist) {
-        const bool exact = mode == ldp::kLDP || mode == ldp::kLDPRaw;  // codes of exactly k bits
+        const bool exact = mode == kLDP || mode == kLDPRaw;  // codes of exactly k bits
         hc.nbins = (exact && compact) ? binom8(k) : 256;
         hc.compact = (exact && compact) ? 1 : 0;
         const size_t bytes = (size_t)R * (size_t)C * (size_t)hc.nbins * sizeof(uint32_t);
         cudaError_t e = cudaMemsetAsync(hist, 0, bytes, s);
-        if (e != cudaSuccess) return cuda_fail(e, "zeroing the histogram");
+        if (e != cudaSuccess) return report_cuda(e, "zeroing the histogram");
     }
-    cudaError_t e = ldp::launch_plain(mode, k, hist != nullptr, plain_variant(H, W), jb, hc, s);
-    if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+    cudaError_t e = launch_plain(mode, k, hist != nullptr, plain_variant(H, W), jb, hc, s);
+    if (e != cudaSuccess) return report_cuda(e, "kernel launch");
     return LDP_OK;
 }
 
-}  // namespace
-
-namespace ldp {
-// Records msg as the calling thread's ldp_last_error() text.
-int report_error(int code, const char* msg) { return fail(code, msg); }
 }  // namespace ldp
+
+using ldp::binom8;
+using ldp::check_codes;
+using ldp::check_image;
+using ldp::run_plain;
+
+namespace {
+int fail(int code, const char* msg) { return ldp::report_error(code, msg); }
+int cuda_fail(cudaError_t e, const char* where) { return ldp::report_cuda(e, where); }
+}  // namespace
 
 struct ldp_batch_plan {
     int mode = 0, k = 3;
@@ -253,164 +265,6 @@ int ldp_region_hist_ex(const uint8_t* d_img, int H, int W, int pitch, int k, int
     if (!d_hist) return fail(LDP_EINVAL, "histogram pointer is NULL");
     return run_plain(mode, d_img, H, W, pitch, k, rs.R, rs.C, rs.compact, d_hist, d_codes_or_null, code_pitch,
                      stream);
-}
-
-int ldp_resize(const uint8_t* d_src, int H, int W, int pitch, int cy, int cx, int ch, int cw, uint8_t* d_dst,
-               int OH, int OW, int dst_pitch, void* stream) {
-    if (!d_src || !d_dst) return fail(LDP_EINVAL, "image pointer is NULL");
-    if (H < 1 || W < 1 || pitch < W) return fail(LDP_EINVAL, "bad source size or pitch");
-    if (H > (1 << 20) || W > (1 << 20)) return fail(LDP_EINVAL, "image side larger than 1<<20");
-    if (ch < 1 || cw < 1 || cy < 0 || cx < 0 || cy + ch > H || cx + cw > W)
-        return fail(LDP_EINVAL, "crop outside the image");
-    if (OH < 1 || OW < 1 || OH > (1 << 16) || OW > (1 << 16)) return fail(LDP_EINVAL, "output size out of range");
-    if (dst_pitch < OW) return fail(LDP_EINVAL, "dst_pitch < OW");
-    int* status = ldp::status_word();
-    if (!status) return fail(LDP_ECUDA, "device status word not found");
-    ldp::Range range("ldp.resize");
-    ldp_crop_desc one{d_src, d_dst, H, W, pitch, cy, cx, ch, cw, dst_pitch};
-    cudaError_t e = ldp::launch_resize(nullptr, &one, 1, OH, OW, status, static_cast<cudaStream_t>(stream));
-    if (e != cudaSuccess) return cuda_fail(e, "resize kernel");
-    return LDP_OK;
-}
-
-int ldp_batch_resize(const ldp_crop_desc* d_descs, int count, int OH, int OW, void* stream) {
-    if (!d_descs) return fail(LDP_EINVAL, "descriptor pointer is NULL");
-    if (count < 1 || count > (1 << 24)) return fail(LDP_EINVAL, "count must be in [1, 1<<24]");
-    if (OH < 1 || OW < 1 || OH > (1 << 16) || OW > (1 << 16)) return fail(LDP_EINVAL, "output size out of range");
-    int* status = ldp::status_word();
-    if (!status) return fail(LDP_ECUDA, "device status word not found");
-    ldp::Range range("ldp.batch_resize");
-    cudaError_t e = ldp::launch_resize(d_descs, nullptr, count, OH, OW, status, static_cast<cudaStream_t>(stream));
-    if (e != cudaSuccess) return cuda_fail(e, "resize kernel");
-    return LDP_OK;
-}
-
-int ldp_hist_distance(const uint32_t* d_q, int nq, int ldq, const uint32_t* d_g, int ng, int ldg, int D,
-                      int metric, void* d_out, int ldo, void* stream) {
-    if (!d_q || !d_g || !d_out) return fail(LDP_EINVAL, "descriptor or output pointer is NULL");
-    if (nq < 1 || ng < 1 || D < 1) return fail(LDP_EINVAL, "nq, ng and D must be at least 1");
-    if (nq > (1 << 22) || ng > (1 << 30)) return fail(LDP_EINVAL, "nq or ng too large");
-    if (ldq < D || ldg < D || ldo < ng) return fail(LDP_EINVAL, "leading dimension too small");
-    if (metric < LDP_DIST_L1 || metric > LDP_DIST_CHI2) return fail(LDP_EINVAL, "metric must be one of LDP_DIST_*");
-    ldp::Range range("ldp.hist_distance");
-    cudaError_t e = ldp::launch_distance(d_q, nq, ldq, d_g, ng, ldg, D, metric, d_out, ldo,
-                                         static_cast<cudaStream_t>(stream));
-    if (e != cudaSuccess) return cuda_fail(e, "distance kernel");
-    return LDP_OK;
-}
-
-int ldp_window_count(int n, int w, int s) {
-    if (w < 1 || s < 1 || n < 0) return -1;
-    return n <= w ? 1 : (n - w + s - 1) / s + 1;
-}
-
-namespace {
-
-int check_windows(const ldp_window_spec& ws, int k) {
-    if (ws.wh < 1 || ws.ww < 1 || ws.sh < 1 || ws.sw < 1)
-        return fail(LDP_EINVAL, "window size and stride must be at least 1");
-    if (ws.compact != 0 && ws.compact != 1) return fail(LDP_EINVAL, "compact must be 0 or 1");
-    if (ws.compact && (k < 1 || k > 7)) return fail(LDP_EINVAL, "compact bins need k in [1,7]");
-    return LDP_OK;
-}
-
-ldp::WindowGeom window_geom(const ldp_window_spec& ws, int k) {
-    ldp::WindowGeom g{ws.wh, ws.ww, ws.sh, ws.sw, 256, k, ws.compact};
-    if (ws.compact) g.nbins = binom8(k);
-    return g;
-}
-
-uint64_t align256(uint64_t b) { return (b + 255u) & ~(uint64_t)255u; }
-
-uint64_t window_scratch(int H, int W, int k, const ldp_window_spec& ws, bool codes_given) {
-    const ldp::WindowGeom g = window_geom(ws, k);
-    uint64_t b = codes_given ? 0 : align256((uint64_t)(H - 2) * (uint64_t)(W - 2));
-    if (!ldp::window_direct(g)) b += ldp::window_cell_words(H, W, g) * sizeof(uint32_t);
-    return b;
-}
-
-int run_windows(int mode, const uint8_t* d_img, int H, int W, int pitch, int k, const ldp_window_spec& ws,
-                uint32_t* d_hist, uint8_t* d_codes, int code_pitch, void* d_scratch, uint64_t scratch_bytes,
-                void* stream) {
-    ldp::Range range("ldp.window_hist");
-    int rc;
-    if ((rc = check_image(d_img, H, W, pitch))) return rc;
-    if ((rc = check_codes(d_codes, W, code_pitch, false))) return rc;
-    if ((rc = check_windows(ws, k))) return rc;
-    if (!d_hist) return fail(LDP_EINVAL, "histogram pointer is NULL");
-    const int nwr = ldp_window_count(H, ws.wh, ws.sh), nwc = ldp_window_count(W, ws.ww, ws.sw);
-    if ((int64_t)nwr * (int64_t)nwc > (1 << 22)) return fail(LDP_EINVAL, "more than 1<<22 windows");
-    const uint64_t need = window_scratch(H, W, k, ws, d_codes != nullptr);
-    if (need && (!d_scratch || scratch_bytes < need)) return fail(LDP_EINVAL, "scratch missing or too small");
-    if (((uintptr_t)d_scratch & 255u) != 0) return fail(LDP_EINVAL, "scratch must be 256-byte aligned");
-    uint8_t* sp = static_cast<uint8_t*>(d_scratch);
-    if (!d_codes) {
-        d_codes = sp;
-        code_pitch = W - 2;
-        sp += align256((uint64_t)(H - 2) * (uint64_t)(W - 2));
-    }
-    if ((rc = run_plain(mode, d_img, H, W, pitch, k < 1 ? 1 : k, 1, 1, 0, nullptr, d_codes, code_pitch, stream)))
-        return rc;
-    ldp_image_desc one{d_img, H, W, pitch, code_pitch, d_codes, 0};
-    cudaError_t e = ldp::launch_windows(nullptr, &one, 1, H, W, window_geom(ws, k), d_hist,
-                                        reinterpret_cast<uint32_t*>(sp), 0, static_cast<cudaStream_t>(stream));
-    if (e != cudaSuccess) return cuda_fail(e, "window kernels");
-    return LDP_OK;
-}
-
-}  // namespace
-
-uint64_t ldp_window_scratch_bytes(int H, int W, int k, ldp_window_spec ws, int codes_given) {
-    if (H < 3 || W < 3 || k < 0 || k > 7 || ws.wh < 1 || ws.ww < 1 || ws.sh < 1 || ws.sw < 1) return 0;
-    if (ws.compact && k < 1) return 0;
-    return window_scratch(H, W, k, ws, codes_given != 0);
-}
-
-int ldp_window_hist(const uint8_t* d_img, int H, int W, int pitch, int k, ldp_window_spec ws, uint32_t* d_hist,
-                    uint8_t* d_codes_or_null, int code_pitch, void* d_scratch, uint64_t scratch_bytes,
-                    void* stream) {
-    if (k < 1 || k > 7) return fail(LDP_EINVAL, "k must be in [1,7]");
-    return run_windows(0, d_img, H, W, pitch, k, ws, d_hist, d_codes_or_null, code_pitch, d_scratch,
-                       scratch_bytes, stream);
-}
-
-int lbp_window_hist(const uint8_t* d_img, int H, int W, int pitch, ldp_window_spec ws, uint32_t* d_hist,
-                    uint8_t* d_codes_or_null, int code_pitch, void* d_scratch, uint64_t scratch_bytes,
-                    void* stream) {
-    if (ws.compact) return fail(LDP_EINVAL, "LBP windows use 256 raw bins (compact = 0)");
-    return run_windows(1, d_img, H, W, pitch, 0, ws, d_hist, d_codes_or_null, code_pitch, d_scratch,
-                       scratch_bytes, stream);
-}
-
-uint64_t ldp_batch_window_scratch_bytes(int count, int max_H, int max_W, int k, ldp_window_spec ws) {
-    if (count < 1 || max_H < 3 || max_W < 3 || k < 0 || k > 7 || ws.wh < 1 || ws.ww < 1 || ws.sh < 1 ||
-        ws.sw < 1 || (ws.compact && k < 1))
-        return 0;
-    const ldp::WindowGeom g = window_geom(ws, k);
-    if (ldp::window_direct(g)) return 0;
-    return (uint64_t)count * ldp::window_cell_words(max_H, max_W, g) * sizeof(uint32_t);
-}
-
-int ldp_batch_window_hist(const ldp_image_desc* d_descs, int count, int max_H, int max_W, int k,
-                          ldp_window_spec ws, uint32_t* d_hist, void* d_scratch, uint64_t scratch_bytes,
-                          void* stream) {
-    int rc;
-    if (!d_descs) return fail(LDP_EINVAL, "descriptor pointer is NULL");
-    if (count < 1 || count > (1 << 24)) return fail(LDP_EINVAL, "count must be in [1, 1<<24]");
-    if (max_H < 3 || max_W < 3 || max_H > (1 << 20) || max_W > (1 << 20))
-        return fail(LDP_EINVAL, "max_H / max_W must be in [3, 1<<20]");
-    if (k < 0 || k > 7) return fail(LDP_EINVAL, "k must be in [0,7]");
-    if ((rc = check_windows(ws, k))) return rc;
-    if (!d_hist) return fail(LDP_EINVAL, "histogram pointer is NULL");
-    ldp::Range range("ldp.batch_window_hist");
-    const ldp::WindowGeom g = window_geom(ws, k);
-    const uint64_t words = ldp::window_direct(g) ? 0 : ldp::window_cell_words(max_H, max_W, g);
-    if (words && (!d_scratch || scratch_bytes < (uint64_t)count * words * sizeof(uint32_t)))
-        return fail(LDP_EINVAL, "scratch missing or too small");
-    cudaError_t e = ldp::launch_windows(d_descs, nullptr, count, max_H, max_W, g, d_hist,
-                                        static_cast<uint32_t*>(d_scratch), words, static_cast<cudaStream_t>(stream));
-    if (e != cudaSuccess) return cuda_fail(e, "window kernels");
-    return LDP_OK;
 }
 
 int ldp_batch_plan_create(ldp_batch_plan** out, int max_images, uint64_t max_pixels, int k, ldp_region_spec rs,

@@ -137,3 +137,22 @@ cudaError_t launch_distance(const uint32_t* q, int nq, int ldq, const uint32_t* 
 }
 
 }  // namespace ldp
+
+// C-ABI entry point (include/ldp.h).
+extern "C" {
+
+int ldp_hist_distance(const uint32_t* d_q, int nq, int ldq, const uint32_t* d_g, int ng, int ldg, int D,
+                      int metric, void* d_out, int ldo, void* stream) {
+    if (!d_q || !d_g || !d_out) return ldp::report_error(LDP_EINVAL, "descriptor or output pointer is NULL");
+    if (nq < 1 || ng < 1 || D < 1) return ldp::report_error(LDP_EINVAL, "nq, ng and D must be at least 1");
+    if (nq > (1 << 22) || ng > (1 << 30)) return ldp::report_error(LDP_EINVAL, "nq or ng too large");
+    if (ldq < D || ldg < D || ldo < ng) return ldp::report_error(LDP_EINVAL, "leading dimension too small");
+    if (metric < LDP_DIST_L1 || metric > LDP_DIST_CHI2) return ldp::report_error(LDP_EINVAL, "metric must be one of LDP_DIST_*");
+    ldp::Range range("ldp.hist_distance");
+    cudaError_t e = ldp::launch_distance(d_q, nq, ldq, d_g, ng, ldg, D, metric, d_out, ldo,
+                                         static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return ldp::report_cuda(e, "distance kernel");
+    return LDP_OK;
+}
+
+}  // extern "C"

@@ -1,5 +1,6 @@
-// Internal interface between the C-ABI layer (ldp_abi.cu) and the kernel
-// translation unit (ldp_kernels.cu).  Not part of the public ABI.
+// Internal interface between the C-ABI files (ldp_abi.cu and the entry points
+// of the feature files) and the kernel translation units.  Not part of the
+// public ABI.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -120,9 +121,25 @@ cudaError_t launch_distance(const uint32_t* q, int nq, int ldq, const uint32_t* 
                             int metric, void* out, int ldo, cudaStream_t s);
 
 cudaError_t read_clear_status(cudaStream_t s, int* out);
-// Records msg as the calling thread's ldp_last_error() text; returns code.
-int report_error(int code, const char* msg);
 // Device address of the status word on the current device (looked up once per device).
 int* status_word();
+
+// Host side of the C-ABI (defined in ldp_abi.cu, used by every file that
+// exports entry points).
+// Records msg as the calling thread's ldp_last_error() text; returns code.
+int report_error(int code, const char* msg);
+// Records "where: <CUDA error name>: <text>"; returns LDP_ECUDA.
+int report_cuda(cudaError_t e, const char* where);
+// C(8, r) for r in [0, 8], else -1: the number of compact bins of k = r.
+int binom8(int r);
+// Argument checks of an image / a code map (required: a NULL map is an
+// error); LDP_OK or LDP_EINVAL with the reason recorded.
+int check_image(const void* img, int H, int W, int pitch);
+int check_codes(const void* codes, int W, int code_pitch, bool required);
+// One single-image launch of kernel mode `mode` (validated arguments): zeroes
+// the R x C histogram (when hist is given) and runs the plain kernel in the
+// tile variant chosen for the image's size.
+int run_plain(int mode, const uint8_t* img, int H, int W, int pitch, int k, int R, int C, int compact,
+              uint32_t* hist, uint8_t* codes, int code_pitch, void* stream);
 
 }  // namespace ldp

@@ -15,7 +15,6 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
-#include <cstdio>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -52,11 +51,7 @@ constexpr size_t kMetaHead = 16;  // count (int32) + padding, keeps the descript
 
 int pfail(int code, const char* msg) { return ldp::report_error(code, msg); }
 
-int pcuda(cudaError_t e, const char* where) {
-    char buf[256];
-    snprintf(buf, sizeof(buf), "%s: %s: %s", where, cudaGetErrorName(e), cudaGetErrorString(e));
-    return ldp::report_error(LDP_ECUDA, buf);
-}
+int pcuda(cudaError_t e, const char* where) { return ldp::report_cuda(e, where); }
 
 void destroy_bufs(ldp_pipeline* p) {
     for (auto& b : p->bufs) {

@@ -141,3 +141,38 @@ cudaError_t launch_resize(const ldp_crop_desc* d_descs, const ldp_crop_desc* one
 }
 
 }  // namespace ldp
+
+// C-ABI entry points (include/ldp.h).
+extern "C" {
+
+int ldp_resize(const uint8_t* d_src, int H, int W, int pitch, int cy, int cx, int ch, int cw, uint8_t* d_dst,
+               int OH, int OW, int dst_pitch, void* stream) {
+    if (!d_src || !d_dst) return ldp::report_error(LDP_EINVAL, "image pointer is NULL");
+    if (H < 1 || W < 1 || pitch < W) return ldp::report_error(LDP_EINVAL, "bad source size or pitch");
+    if (H > (1 << 20) || W > (1 << 20)) return ldp::report_error(LDP_EINVAL, "image side larger than 1<<20");
+    if (ch < 1 || cw < 1 || cy < 0 || cx < 0 || cy + ch > H || cx + cw > W)
+        return ldp::report_error(LDP_EINVAL, "crop outside the image");
+    if (OH < 1 || OW < 1 || OH > (1 << 16) || OW > (1 << 16)) return ldp::report_error(LDP_EINVAL, "output size out of range");
+    if (dst_pitch < OW) return ldp::report_error(LDP_EINVAL, "dst_pitch < OW");
+    int* status = ldp::status_word();
+    if (!status) return ldp::report_error(LDP_ECUDA, "device status word not found");
+    ldp::Range range("ldp.resize");
+    ldp_crop_desc one{d_src, d_dst, H, W, pitch, cy, cx, ch, cw, dst_pitch};
+    cudaError_t e = ldp::launch_resize(nullptr, &one, 1, OH, OW, status, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return ldp::report_cuda(e, "resize kernel");
+    return LDP_OK;
+}
+
+int ldp_batch_resize(const ldp_crop_desc* d_descs, int count, int OH, int OW, void* stream) {
+    if (!d_descs) return ldp::report_error(LDP_EINVAL, "descriptor pointer is NULL");
+    if (count < 1 || count > (1 << 24)) return ldp::report_error(LDP_EINVAL, "count must be in [1, 1<<24]");
+    if (OH < 1 || OW < 1 || OH > (1 << 16) || OW > (1 << 16)) return ldp::report_error(LDP_EINVAL, "output size out of range");
+    int* status = ldp::status_word();
+    if (!status) return ldp::report_error(LDP_ECUDA, "device status word not found");
+    ldp::Range range("ldp.batch_resize");
+    cudaError_t e = ldp::launch_resize(d_descs, nullptr, count, OH, OW, status, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return ldp::report_cuda(e, "resize kernel");
+    return LDP_OK;
+}
+
+}  // extern "C"

@@ -24,10 +24,6 @@
 
 #include "ldp_launch.h"
 
-namespace ldp {
-int report_error(int code, const char* msg);
-}
-
 namespace {
 
 uint64_t now_ns() {

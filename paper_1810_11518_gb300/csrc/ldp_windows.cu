@@ -298,3 +298,123 @@ cudaError_t launch_windows(const ldp_image_desc* d_descs, const ldp_image_desc* 
 }
 
 }  // namespace ldp
+
+// C-ABI entry points (include/ldp.h): argument checks, scratch sizes, the
+// code pass of single images (run_plain) followed by the window kernels.
+extern "C" {
+
+int ldp_window_count(int n, int w, int s) {
+    if (w < 1 || s < 1 || n < 0) return -1;
+    return n <= w ? 1 : (n - w + s - 1) / s + 1;
+}
+
+namespace {
+
+int check_windows(const ldp_window_spec& ws, int k) {
+    if (ws.wh < 1 || ws.ww < 1 || ws.sh < 1 || ws.sw < 1)
+        return ldp::report_error(LDP_EINVAL, "window size and stride must be at least 1");
+    if (ws.compact != 0 && ws.compact != 1) return ldp::report_error(LDP_EINVAL, "compact must be 0 or 1");
+    if (ws.compact && (k < 1 || k > 7)) return ldp::report_error(LDP_EINVAL, "compact bins need k in [1,7]");
+    return LDP_OK;
+}
+
+ldp::WindowGeom window_geom(const ldp_window_spec& ws, int k) {
+    ldp::WindowGeom g{ws.wh, ws.ww, ws.sh, ws.sw, 256, k, ws.compact};
+    if (ws.compact) g.nbins = ldp::binom8(k);
+    return g;
+}
+
+uint64_t align256(uint64_t b) { return (b + 255u) & ~(uint64_t)255u; }
+
+uint64_t window_scratch(int H, int W, int k, const ldp_window_spec& ws, bool codes_given) {
+    const ldp::WindowGeom g = window_geom(ws, k);
+    uint64_t b = codes_given ? 0 : align256((uint64_t)(H - 2) * (uint64_t)(W - 2));
+    if (!ldp::window_direct(g)) b += ldp::window_cell_words(H, W, g) * sizeof(uint32_t);
+    return b;
+}
+
+int run_windows(int mode, const uint8_t* d_img, int H, int W, int pitch, int k, const ldp_window_spec& ws,
+                uint32_t* d_hist, uint8_t* d_codes, int code_pitch, void* d_scratch, uint64_t scratch_bytes,
+                void* stream) {
+    ldp::Range range("ldp.window_hist");
+    int rc;
+    if ((rc = ldp::check_image(d_img, H, W, pitch))) return rc;
+    if ((rc = ldp::check_codes(d_codes, W, code_pitch, false))) return rc;
+    if ((rc = check_windows(ws, k))) return rc;
+    if (!d_hist) return ldp::report_error(LDP_EINVAL, "histogram pointer is NULL");
+    const int nwr = ldp_window_count(H, ws.wh, ws.sh), nwc = ldp_window_count(W, ws.ww, ws.sw);
+    if ((int64_t)nwr * (int64_t)nwc > (1 << 22)) return ldp::report_error(LDP_EINVAL, "more than 1<<22 windows");
+    const uint64_t need = window_scratch(H, W, k, ws, d_codes != nullptr);
+    if (need && (!d_scratch || scratch_bytes < need)) return ldp::report_error(LDP_EINVAL, "scratch missing or too small");
+    if (((uintptr_t)d_scratch & 255u) != 0) return ldp::report_error(LDP_EINVAL, "scratch must be 256-byte aligned");
+    uint8_t* sp = static_cast<uint8_t*>(d_scratch);
+    if (!d_codes) {
+        d_codes = sp;
+        code_pitch = W - 2;
+        sp += align256((uint64_t)(H - 2) * (uint64_t)(W - 2));
+    }
+    if ((rc = ldp::run_plain(mode, d_img, H, W, pitch, k < 1 ? 1 : k, 1, 1, 0, nullptr, d_codes, code_pitch, stream)))
+        return rc;
+    ldp_image_desc one{d_img, H, W, pitch, code_pitch, d_codes, 0};
+    cudaError_t e = ldp::launch_windows(nullptr, &one, 1, H, W, window_geom(ws, k), d_hist,
+                                        reinterpret_cast<uint32_t*>(sp), 0, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return ldp::report_cuda(e, "window kernels");
+    return LDP_OK;
+}
+
+}  // namespace
+
+uint64_t ldp_window_scratch_bytes(int H, int W, int k, ldp_window_spec ws, int codes_given) {
+    if (H < 3 || W < 3 || k < 0 || k > 7 || ws.wh < 1 || ws.ww < 1 || ws.sh < 1 || ws.sw < 1) return 0;
+    if (ws.compact && k < 1) return 0;
+    return window_scratch(H, W, k, ws, codes_given != 0);
+}
+
+int ldp_window_hist(const uint8_t* d_img, int H, int W, int pitch, int k, ldp_window_spec ws, uint32_t* d_hist,
+                    uint8_t* d_codes_or_null, int code_pitch, void* d_scratch, uint64_t scratch_bytes,
+                    void* stream) {
+    if (k < 1 || k > 7) return ldp::report_error(LDP_EINVAL, "k must be in [1,7]");
+    return run_windows(0, d_img, H, W, pitch, k, ws, d_hist, d_codes_or_null, code_pitch, d_scratch,
+                       scratch_bytes, stream);
+}
+
+int lbp_window_hist(const uint8_t* d_img, int H, int W, int pitch, ldp_window_spec ws, uint32_t* d_hist,
+                    uint8_t* d_codes_or_null, int code_pitch, void* d_scratch, uint64_t scratch_bytes,
+                    void* stream) {
+    if (ws.compact) return ldp::report_error(LDP_EINVAL, "LBP windows use 256 raw bins (compact = 0)");
+    return run_windows(1, d_img, H, W, pitch, 0, ws, d_hist, d_codes_or_null, code_pitch, d_scratch,
+                       scratch_bytes, stream);
+}
+
+uint64_t ldp_batch_window_scratch_bytes(int count, int max_H, int max_W, int k, ldp_window_spec ws) {
+    if (count < 1 || max_H < 3 || max_W < 3 || k < 0 || k > 7 || ws.wh < 1 || ws.ww < 1 || ws.sh < 1 ||
+        ws.sw < 1 || (ws.compact && k < 1))
+        return 0;
+    const ldp::WindowGeom g = window_geom(ws, k);
+    if (ldp::window_direct(g)) return 0;
+    return (uint64_t)count * ldp::window_cell_words(max_H, max_W, g) * sizeof(uint32_t);
+}
+
+int ldp_batch_window_hist(const ldp_image_desc* d_descs, int count, int max_H, int max_W, int k,
+                          ldp_window_spec ws, uint32_t* d_hist, void* d_scratch, uint64_t scratch_bytes,
+                          void* stream) {
+    int rc;
+    if (!d_descs) return ldp::report_error(LDP_EINVAL, "descriptor pointer is NULL");
+    if (count < 1 || count > (1 << 24)) return ldp::report_error(LDP_EINVAL, "count must be in [1, 1<<24]");
+    if (max_H < 3 || max_W < 3 || max_H > (1 << 20) || max_W > (1 << 20))
+        return ldp::report_error(LDP_EINVAL, "max_H / max_W must be in [3, 1<<20]");
+    if (k < 0 || k > 7) return ldp::report_error(LDP_EINVAL, "k must be in [0,7]");
+    if ((rc = check_windows(ws, k))) return rc;
+    if (!d_hist) return ldp::report_error(LDP_EINVAL, "histogram pointer is NULL");
+    ldp::Range range("ldp.batch_window_hist");
+    const ldp::WindowGeom g = window_geom(ws, k);
+    const uint64_t words = ldp::window_direct(g) ? 0 : ldp::window_cell_words(max_H, max_W, g);
+    if (words && (!d_scratch || scratch_bytes < (uint64_t)count * words * sizeof(uint32_t)))
+        return ldp::report_error(LDP_EINVAL, "scratch missing or too small");
+    cudaError_t e = ldp::launch_windows(d_descs, nullptr, count, max_H, max_W, g, d_hist,
+                                        static_cast<uint32_t*>(d_scratch), words, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return ldp::report_cuda(e, "window kernels");
+    return LDP_OK;
+}
+
+}  // extern "C"
