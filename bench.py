@@ -78,9 +78,9 @@ def dist_env():
 # profiles/k_batch_ldp_k3_512img_full.md), scaled to a launch by its pixels.
 # Valid only for the kernel sources it was taken on: any change to them
 # reports traffic as null until a new capture is recorded here.
-TRAFFIC_PER_PX = 300.845e6 / (512 * 640 * 490)
+TRAFFIC_PER_PX = 300.021e6 / (512 * 640 * 490)
 TRAFFIC_SOURCES = ("paper_1810_11518_gb300/csrc/ldp_device.cuh", "paper_1810_11518_gb300/csrc/ldp_kernels.cu")
-TRAFFIC_SHA256 = "3959def2b06b711858a923d721ed65f35ac51672048ab56cf81642b1b4425321"
+TRAFFIC_SHA256 = "815e12e83717dc219d3386188adced54c3020a23bbd9a8a13f21a75b77ed4f13"
 
 
 def measured_traffic(pixels, k, H, W):
@@ -226,9 +226,11 @@ def time_batch(ldp, torch, dev, Hs, Ws, seeds, ks, regions, sigma, steps, tune=T
     return out
 
 
-def time_windows(ldp, torch, dev, n, H, W, k, window, stride, steps):
+def time_windows(ldp, torch, dev, n, H, W, k, window, stride, steps, peak):
     """Sliding-window leg (Sec. 3.2): one batch plan run storing the codes of
-    n H x W images, then the window histograms of all of them in one call."""
+    n H x W images, then the window histograms of all of them in one call.
+    The window pass alone is also reported against HBM: its algorithmic bytes
+    are the code maps read and the window histograms written."""
     import synth
     from paper_1810_11518_gb300 import autotune
 
@@ -275,10 +277,13 @@ def time_windows(ldp, torch, dev, n, H, W, k, window, stride, steps):
             e1.record()
             torch.cuda.synchronize(dev)
             tw += e0.elapsed_time(e1)
+    pass_bytes = n * ((H - 2) * (W - 2) + per * 4)
+    pass_gbs = pass_bytes / (tw / steps * 1e-3) / 1e9
     return {"images": n, "height": H, "width": W, "k": k, "window": list(window),
             "stride": list(window if stride is None else stride), "windows_per_image": nwin,
             "ms_per_step": round(ms, 4), "value": round(lay.pixels / (ms * 1e-3) / 1e6, 3), "unit": UNIT,
-            "window_pass_ms": round(tw / steps, 4)}
+            "window_pass_ms": round(tw / steps, 4), "window_pass_bytes": pass_bytes,
+            "window_pass_gbs": round(pass_gbs, 1), "window_pass_hbm_frac": round(pass_gbs / peak, 4)}
 
 
 def time_face_pipeline(ldp, torch, dev, lay, d_img, k, steps, seed=7):
@@ -613,8 +618,8 @@ def main():
         extras["distances"] = time_distances(ldp, torch, dev, d_hist, n, hist_len, 5)
         extras["face_pipeline"] = time_face_pipeline(ldp, torch, dev, lay, d_img, k, max(5, a.steps // 10))
         extras["windows"] = [
-            time_windows(ldp, torch, dev, n, 260, 260, k, (20, 20), None, max(5, a.steps // 10)),
-            time_windows(ldp, torch, dev, n, H, W, k, (20, 20), (10, 10), max(5, a.steps // 10)),
+            time_windows(ldp, torch, dev, n, 260, 260, k, (20, 20), None, max(5, a.steps // 10), peak),
+            time_windows(ldp, torch, dev, n, H, W, k, (20, 20), (10, 10), max(5, a.steps // 10), peak),
         ]
     if a.large and rank == 0:
         # ---- large images: 64 x 8192^2 (sigma 6), 16x16 regions, k = 1..4 ----

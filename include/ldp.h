@@ -227,9 +227,11 @@ LDP_API uint64_t ldp_batch_window_scratch_bytes(int count, int max_H, int max_W,
 /* Window histograms of `count` images (host value) from code maps already
  * in device memory, e.g. stored by ldp_batch_run: image i is d_descs[i]
  * (codes, code_pitch, H, W; img unused), its windows go to
- * d_hist + hist_offset.  Every image must satisfy H <= max_H, W <= max_W;
- * images with codes == NULL are skipped.  k >= 1 with ws.compact = 1:
- * C(8,k) bins; else 256 raw bins (k = 0 for LBP maps). */
+ * d_hist + hist_offset.  Every image must satisfy 3 <= H <= max_H,
+ * 3 <= W <= max_W and code_pitch >= W - 2: one that does not is skipped
+ * and sets bit 0 of the device status word (ldp_device_status); images with
+ * codes == NULL are skipped.  k >= 1 with ws.compact = 1: C(8,k) bins; else
+ * 256 raw bins (k = 0 for LBP maps). */
 LDP_API int ldp_batch_window_hist(const ldp_image_desc *d_descs, int count, int max_H, int max_W, int k,
                                   ldp_window_spec ws, uint32_t *d_hist, void *d_scratch, uint64_t scratch_bytes,
                                   void *stream);

@@ -413,8 +413,11 @@ __device__ __forceinline__ int band_lo(int b, int n, int nb) {
 // Input rows come either from per-lane global loads one row ahead, or
 // (STAGED, for 16-byte aligned images) from the warp's bulk-copy ring, two
 // stages ahead.  With HIST the codes are counted in the warp's private shared
-// histogram `wh` (kWarpSlots x 256 raw bins, all zero on entry and on exit):
-// the flush adds every non-zero bin to the global histogram and resets it.
+// histogram `wh` (kWarpSlots x 256 raw bins; every bin the flush reads is
+// zero on entry and on exit): the flush adds every non-zero bin to the global
+// histogram and resets it.  In the LDP modes bin 0 of a slot (code 0, which
+// they never produce) takes the counts of columns past the interior and is
+// never read.
 // Region grids too fine for kWarpSlots slots count straight into global
 // memory.  `ph` holds the ring's per-stage wait parities across tiles.
 template <int MODE, int K, int RW, bool HIST, bool STAGED>
@@ -452,9 +455,15 @@ __device__ __forceinline__ void warp_tile(const Job& jb, const HistCfg& hc, int 
     const bool fast_st = cod_al && (v + 4 <= W - 2);
     bool valid[4];
     int colb[4];  // per column: slot offset (smem) or region column (global)
+    // byte_perm selector of column t's code for the shared histogram; a
+    // column past the interior reads a zero byte instead: code 0 never occurs
+    // in the LDP modes (at least one bit is set), so its bin is never flushed
+    // and the count needs no branch
+    uint32_t csel[4];
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
         valid[t] = v + t < W - 2;
+        csel[t] = valid[t] ? (0x4440u | (uint32_t)t) : 0x4444u;
         colb[t] = 0;
         if (HIST && valid[t]) {
             const int rj = band_of(v + t + 1, W, hc.C);
@@ -499,14 +508,13 @@ __device__ __forceinline__ void warp_tile(const Job& jb, const HistCfg& hc, int 
                 // LDP codes spread over the bins: one byte extract, one
                 // multiply-add for the address, one reduction per pixel
 #pragma unroll
-                for (int t = 0; t < 4; ++t)
-                    if (valid[t]) {
-                        const uint32_t code = prmt(packed, 0u, 0x4440u | (uint32_t)t);
-                        uint32_t addr;
-                        asm("mad.lo.u32 %0, %1, 4, %2;" : "=r"(addr) : "r"(code), "r"(sbase[t]));
-                        if (index_ok(addr - wh_addr < 4u * kWarpSlots * 256u, status))
-                            asm volatile("red.shared.add.u32 [%0], 1;" ::"r"(addr) : "memory");
-                    }
+                for (int t = 0; t < 4; ++t) {
+                    const uint32_t code = prmt(packed, 0u, csel[t]);
+                    uint32_t addr;
+                    asm("mad.lo.u32 %0, %1, 4, %2;" : "=r"(addr) : "r"(code), "r"(sbase[t]));
+                    if (index_ok(addr - wh_addr < 4u * kWarpSlots * 256u, status))
+                        asm volatile("red.shared.add.u32 [%0], 1;" ::"r"(addr) : "memory");
+                }
             } else if (use_smem) {
                 // LBP: neighbouring lanes often share a code (flat areas give
                 // 255); the compiler's shared atomicAdd is faster there
@@ -635,20 +643,27 @@ __device__ __forceinline__ void warp_tile(const Job& jb, const HistCfg& hc, int 
         Row r0, r1, r2;
         unpack(load_raw(rp, v, W, fast_ld), r0);
         unpack(load_raw(rp + P, v, W, fast_ld), r1);
-        auto step = [&](const Row& A, const Row& B, Row& C, int u) {
+        // ALWAYS: the next output row exists, so the prefetch needs no test
+        auto step = [&](const Row& A, const Row& B, Row& C, int u, auto always) {
             unpack(nx, C);
-            if (u + 1 < ue && index_ok(u + 3 < H, status)) nx = load_raw(pf, v, W, fast_ld);
+            if (decltype(always)::value ? index_ok(u + 3 < H, status)
+                                        : (u + 1 < ue && index_ok(u + 3 < H, status)))
+                nx = load_raw(pf, v, W, fast_ld);
             pf += P;
             emit(u, codes_of_row(A, B, C));
         };
+        const std::true_type yes;
+        const std::false_type no;
         int u = u0;
-        for (; u + 3 <= ue; u += 3) {
-            step(r0, r1, r2, u);
-            step(r1, r2, r0, u + 1);
-            step(r2, r0, r1, u + 2);
+        for (; u + 4 <= ue; u += 3) {
+            step(r0, r1, r2, u, yes);
+            step(r1, r2, r0, u + 1, yes);
+            step(r2, r0, r1, u + 2, yes);
         }
-        if (u < ue) step(r0, r1, r2, u);
-        if (u + 1 < ue) step(r1, r2, r0, u + 1);
+        // one to three rows left
+        if (u < ue) step(r0, r1, r2, u, no);
+        if (u + 1 < ue) step(r1, r2, r0, u + 1, no);
+        if (u + 2 < ue) step(r2, r0, r1, u + 2, no);
     }
 
     if constexpr (HIST) {
@@ -664,7 +679,9 @@ __device__ __forceinline__ void warp_tile(const Job& jb, const HistCfg& hc, int 
 #pragma unroll
             for (int m = 0; m < NI; ++m) {
                 const int idx = lane + 32 * m;
-                code_of[m] = exact_k(MODE) ? (idx < NC ? (int)__ldg(&g_code_list.code[K][idx]) : -1) : idx;
+                // (code 0 of the LDP threshold modes holds the skipped columns)
+                code_of[m] = exact_k(MODE) ? (idx < NC ? (int)__ldg(&g_code_list.code[K][idx]) : -1)
+                                           : ((is_ldp(MODE) && idx == 0) ? -1 : idx);
             }
             for (int sl = 0; sl < nslots; ++sl) {
                 const int hbase = ((ri_lo + sl / ncs) * hc.C + rj_lo + sl % ncs) * hc.nbins;

@@ -99,14 +99,15 @@ struct WindowGeom {
     int wh, ww, sh, sw;
     int nbins, k, compact;
 };
-// uint32 words of the cell histograms of one H x W image
+// uint32 words of the cell histograms of one H x W image: 0 when no cell
+// scratch is needed (stride = size, or the fused single pass applies)
 uint64_t window_cell_words(int H, int W, const WindowGeom& g);
 // stride = size: the cells are the windows (no cell scratch, no sum pass)
 bool window_direct(const WindowGeom& g);
 // Window histograms of `count` images from their code maps: descriptors in
 // device memory (d_descs) or one by value (one, count = 1); max_H / max_W
 // bound the images' sizes; cells: scratch of cell_stride words per image
-// (unused when window_direct).
+// (unused when window_cell_words is 0).
 cudaError_t launch_windows(const ldp_image_desc* d_descs, const ldp_image_desc* one, int count, int max_H,
                            int max_W, const WindowGeom& g, uint32_t* hist, uint32_t* cells,
                            uint64_t cell_stride, cudaStream_t s);

@@ -12,11 +12,18 @@
 //                  exactly one CTA);
 //   k_window_sum:  each window histogram is the sum of its cells' (skipped
 //                  when stride = size: the cells are the windows).
+// When the column stride divides the window width (cells as wide as the
+// stride) and qh rows of cells fit in shared memory, k_window_fused does both
+// in one pass instead: a CTA walks an image's window rows top to bottom in
+// groups, counts each cell row once into a shared-memory ring that holds the
+// cell rows of the current group, and writes the group's window rows
+// straight from the ring -- the cell histograms never reach HBM.
 // Images come from ldp_image_desc records (batches) or one record passed by
 // value (single image).
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "ldp_device.cuh"
 #include "ldp_launch.h"
@@ -38,10 +45,20 @@ struct CellArgs {
     uint32_t* hist;    // window histograms (direct) ...
     uint32_t* cells;   // ... or cell histograms, image i at cells + i * cell_stride
     uint64_t cell_stride;
+    int max_H, max_W;  // bounds of the images' sizes
+    int* status;       // device status word
 };
 
 __device__ __forceinline__ ldp_image_desc desc_of(const CellArgs& a, int i) {
     return a.descs ? a.descs[i] : a.one;
+}
+
+// An image outside the call's size bounds (or without interior pixels, or
+// with a short code pitch) is skipped and sets bit 0 of the status word.
+__device__ __forceinline__ bool win_desc_ok(const ldp_image_desc& d, int max_H, int max_W, int* status) {
+    const bool ok = d.H >= 3 && d.W >= 3 && d.H <= max_H && d.W <= max_W && d.code_pitch >= d.W - 2;
+    if (!ok && threadIdx.x == 0) atomicOr(status, 1);
+    return ok;
 }
 
 // Cell of column y: y / cw, from a float estimate corrected by one step
@@ -69,10 +86,11 @@ __global__ void __launch_bounds__(kCellThreads) k_cell_hist(CellArgs a, int coun
     for (uint64_t p = blockIdx.x; p < pairs; p += gridDim.x) {
         const int img = (int)(p / (uint64_t)ncr_max), i = (int)(p % (uint64_t)ncr_max);
         const ldp_image_desc d = desc_of(a, img);
+        if (d.codes == nullptr || !win_desc_ok(d, a.max_H, a.max_W, a.status)) continue;  // uniform over the CTA
         const int H = d.H, W = d.W;
         const int ncr = (H + a.ch - 1) / a.ch, ncc = (W + a.cw - 1) / a.cw;
         const int j0 = blockIdx.y * a.chunk;
-        if (i >= ncr || j0 >= ncc || d.codes == nullptr) continue;  // uniform over the CTA
+        if (i >= ncr || j0 >= ncc) continue;  // uniform over the CTA
         const int j1 = min(j0 + a.chunk, ncc);
         const int words = (j1 - j0) * a.nbins;
         __syncthreads();  // lut ready; the previous item's counters are stored
@@ -131,7 +149,7 @@ __global__ void __launch_bounds__(kCellThreads) k_cell_hist_image(CellArgs a, in
     const float inv_cw = 1.0f / (float)a.cw, inv_ch = 1.0f / (float)a.ch;
     for (int img = blockIdx.x; img < count; img += gridDim.x) {
         const ldp_image_desc d = desc_of(a, img);
-        if (d.codes == nullptr) continue;  // uniform over the CTA
+        if (d.codes == nullptr || !win_desc_ok(d, a.max_H, a.max_W, a.status)) continue;  // uniform over the CTA
         const int H = d.H, W = d.W;
         const int ncc = (W + a.cw - 1) / a.cw;
         const int words = ((H + a.ch - 1) / a.ch) * ncc * a.nbins;
@@ -183,6 +201,8 @@ struct SumArgs {
     const uint32_t* cells;
     uint64_t cell_stride;
     uint32_t* hist;
+    int max_H, max_W;
+    int* status;
 };
 
 __device__ __forceinline__ int win_count(int n, int w, int s) { return n <= w ? 1 : (n - w + s - 1) / s + 1; }
@@ -196,6 +216,8 @@ __global__ void __launch_bounds__(256) k_window_sum(SumArgs a, int count, int nw
     for (uint64_t it = blockIdx.x; it < items; it += gridDim.x) {
         const int img = (int)(it / (uint64_t)nwr_max), wa = (int)(it % (uint64_t)nwr_max);
         const ldp_image_desc d = a.descs ? a.descs[img] : a.one;
+        // images without codes have no cells (the counting pass skipped them)
+        if (d.codes == nullptr || !win_desc_ok(d, a.max_H, a.max_W, a.status)) continue;
         const int H = d.H, W = d.W;
         const int nwr = win_count(H, a.wh, a.sh);
         if (wa >= nwr) continue;
@@ -218,6 +240,204 @@ __global__ void __launch_bounds__(256) k_window_sum(SumArgs a, int count, int nw
     }
 }
 
+constexpr int kFusedThreads = 512;
+constexpr int kFusedSmemWords = 40960;    // ring counters at most (160 KB)
+constexpr int kFusedGroupWords = 16384;   // ring size up to which window rows are grouped (64 KB)
+constexpr int kFusedMaxGroup = 8;         // window rows per group at most
+
+struct FusedArgs {
+    const ldp_image_desc* descs;  // nullptr: the single image `one`
+    ldp_image_desc one;
+    int ch, cw;          // cell size in pixels; cw is the column stride
+    int qh, qw;          // window size in cells
+    int ph;              // row stride in cells
+    int wh, ww, sh, sw;  // window size and stride in pixels (window counts)
+    int nbins, k;        // as in CellArgs
+    int row_stride;      // ring words per cell row: (cells of the widest image, at least qw) x nbins, rounded to 4
+    int group;           // window rows per group (G)
+    int nslots;          // ring rows: (G - 1) * ph + qh
+    int rows_per_band;   // window rows per work item
+    int bands;           // work items per image
+    uint32_t* hist;
+    int max_H, max_W;    // bounds of the images' sizes (the ring is sized for max_W)
+    int* status;
+};
+
+// Work item = (image, band of window rows).  The band is walked in groups of
+// G window rows.  Per group: the cell rows the group covers that are not yet
+// in the ring are zeroed and counted (ring slot = cell row mod nslots; the
+// nslots = (G-1) ph + qh rows of a group are distinct mod nslots, rows past
+// the image stay out), then every output word e = b*nbins + bin of each of
+// the G window rows is the sum over the window row's cell rows of the ring
+// words e + c*nbins, c < qw (window b covers cells b .. b+qw-1 of the row;
+// cells past the image are zero).  Three barriers per group.  Each warp
+// counts one column block of 128 columns (a lane's four consecutive
+// columns, their cells found once per image) on every rpw-th image row of
+// the group, four rows' loads in flight; wider images loop over blocks.
+// Counts are shared-memory reductions without a branch (a column past the
+// image or a code without a bin counts into a junk word past the ring).
+__global__ void __launch_bounds__(kFusedThreads, 2) k_window_fused(FusedArgs a, int count) {
+    extern __shared__ uint4 ring4[];  // nslots x row_stride counters, then 4 junk words
+    uint32_t* ring = reinterpret_cast<uint32_t*>(ring4);
+    __shared__ int16_t lut[256];
+    for (int c = threadIdx.x; c < 256; c += blockDim.x)
+        lut[c] = (a.k >= 1) ? __ldg(&g_bin_table.bin[a.k][c]) : (int16_t)c;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const float inv_cw = 1.0f / (float)a.cw, inv_ch = 1.0f / (float)a.ch;
+    const int rs = a.row_stride, ns = a.nslots;
+    // one word past the ring takes the counts of columns past the image and of
+    // codes without a bin, so the count needs no branch
+    const uint32_t junk_addr = (uint32_t)__cvta_generic_to_shared(ring + ns * rs);
+    const uint64_t items = (uint64_t)count * (uint64_t)a.bands;
+    for (uint64_t it = blockIdx.x; it < items; it += gridDim.x) {
+        const int img = (int)(it / (uint64_t)a.bands), band = (int)(it % (uint64_t)a.bands);
+        const ldp_image_desc d = a.descs ? a.descs[img] : a.one;
+        if (d.codes == nullptr || !win_desc_ok(d, a.max_H, a.max_W, a.status)) continue;  // uniform over the CTA
+        const int H = d.H, W = d.W;
+        const int nwr = win_count(H, a.wh, a.sh), nwc = win_count(W, a.ww, a.sw);
+        const int a0 = band * a.rows_per_band, a1 = min(a0 + a.rows_per_band, nwr);
+        if (a0 >= a1) continue;
+        const int ncr = (H + a.ch - 1) / a.ch;
+        const int words = nwc * a.nbins;
+        uint32_t* out_img = a.hist + d.hist_offset;
+        const bool vec = (a.nbins & 3) == 0 && ((reinterpret_cast<uintptr_t>(out_img) & 15u) == 0);
+        const bool al = ((reinterpret_cast<uintptr_t>(d.codes) | (uintptr_t)d.code_pitch) & 3u) == 0;
+        const int ncb = (W - 2 + 127) / 128;
+        const bool single = ncb <= nwarps;
+        const int rpw = single ? nwarps / ncb : 1;
+
+        auto block_cells = [&](int cb, int(&off)[4], bool(&in)[4]) {
+            const int yq = 1 + cb * 128 + 4 * lane;  // columns yq .. yq+3
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                in[t] = yq + t < W - 1;
+                off[t] = in[t] ? cell_of(yq + t, a.cw, inv_cw) * a.nbins : 0;
+            }
+        };
+        // image rows x0, x0 + step, ... < x1 of column block cb, each into the
+        // ring row of its cell row (cell rows n0 .. n0 + nslots - 1; n0 in
+        // ring row s_n0)
+        auto count_rows = [&](int cb, const int(&off)[4], const bool(&in)[4], int x0, int x1, int step, int n0,
+                              int s_n0) {
+            const int yq = 1 + cb * 128 + 4 * lane;
+            const bool v4 = al && in[3];
+            const uint8_t* base = d.codes + (yq - 1);
+            for (int x = x0; x < x1; x += 4 * step) {
+                uint32_t w[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int xx = x + j * step;
+                    const uint8_t* cp = base + (size_t)(xx - 1) * (size_t)d.code_pitch;
+                    w[j] = 0;
+                    if (xx < x1) {
+                        if (v4) {
+                            w[j] = __ldg(reinterpret_cast<const unsigned int*>(cp));
+                        } else {
+#pragma unroll
+                            for (int t = 0; t < 4; ++t)
+                                if (in[t]) w[j] |= (uint32_t)__ldg(cp + t) << (8 * t);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int xx = x + j * step;
+                    if (xx < x1) {
+                        int sl = s_n0 + (cell_of(xx, a.ch, inv_ch) - n0);
+                        if (sl >= ns) sl -= ns;
+                        uint32_t* slot = ring + sl * rs;
+                        const uint32_t slot_addr = (uint32_t)__cvta_generic_to_shared(slot);
+#pragma unroll
+                        for (int t = 0; t < 4; ++t) {
+                            const int b = lut[(w[j] >> (8 * t)) & 0xFFu];
+                            const uint32_t addr =
+                                (in[t] && b >= 0) ? slot_addr + 4u * (uint32_t)(off[t] + b) : junk_addr;
+                            asm volatile("red.shared.add.u32 [%0], 1;" ::"r"(addr) : "memory");
+                        }
+                    }
+                }
+            }
+        };
+        int my_off[4] = {0, 0, 0, 0};
+        bool my_in[4] = {false, false, false, false};
+        const int my_cb = warp % ncb, my_phase = warp / ncb;
+        if (single) block_cells(my_cb, my_off, my_in);
+
+        int next = a0 * a.ph;  // first cell row not in the ring
+        for (int g0 = a0; g0 < a1; g0 += a.group) {
+            const int g1 = min(g0 + a.group, a1);  // window rows [g0, g1)
+            const int n0 = max(next, g0 * a.ph);
+            const int n1 = min((g1 - 1) * a.ph + a.qh, ncr);  // cell rows to count: [n0, n1)
+            __syncthreads();  // the previous group's reads of the ring are done
+            for (int r = n0; r < n1; ++r) {
+                uint4* sl = reinterpret_cast<uint4*>(ring + (r % ns) * rs);
+                for (int e = threadIdx.x; e < rs / 4; e += blockDim.x) sl[e] = make_uint4(0, 0, 0, 0);
+            }
+            __syncthreads();
+            if (n0 < n1) {
+                // image rows of cell rows [n0, n1) that hold codes
+                const int x0 = max(n0 * a.ch, 1), x1 = min(n1 * a.ch, H - 1);
+                const int s_n0 = n0 % ns;
+                if (single) {
+                    if (my_phase < rpw) count_rows(my_cb, my_off, my_in, x0 + my_phase, x1, rpw, n0, s_n0);
+                } else {
+                    for (int cb = warp; cb < ncb; cb += nwarps) {
+                        int off[4];
+                        bool in[4];
+                        block_cells(cb, off, in);
+                        count_rows(cb, off, in, x0, x1, 1, n0, s_n0);
+                    }
+                }
+            }
+            next = max(next, n1);
+            __syncthreads();
+            for (int wa = g0; wa < g1; ++wa) {
+                const int r0 = wa * a.ph, nr = min(a.qh, ncr - r0), s0 = r0 % ns;
+                uint32_t* out = out_img + (uint64_t)wa * (uint64_t)words;
+                // QW: qw when it is a small constant (unrolled), else 0 (a loop)
+                auto emit_vec = [&](auto qw_c) {
+                    constexpr int QW = decltype(qw_c)::value;
+                    for (int e = 4 * threadIdx.x; e < words; e += 4 * blockDim.x) {
+                        uint4 acc = make_uint4(0, 0, 0, 0);
+                        int sidx = s0;
+                        for (int ri = 0; ri < nr; ++ri) {
+                            const uint32_t* sl = ring + sidx * rs + e;
+#pragma unroll
+                            for (int c = 0; c < (QW ? QW : a.qw); ++c) {
+                                const uint4 v = *reinterpret_cast<const uint4*>(sl + c * a.nbins);
+                                acc.x += v.x;
+                                acc.y += v.y;
+                                acc.z += v.z;
+                                acc.w += v.w;
+                            }
+                            if (++sidx == ns) sidx = 0;
+                        }
+                        __stcs(reinterpret_cast<uint4*>(out + e), acc);
+                    }
+                };
+                if (vec) {
+                    if (a.qw == 1) emit_vec(std::integral_constant<int, 1>{});
+                    else if (a.qw == 2) emit_vec(std::integral_constant<int, 2>{});
+                    else if (a.qw == 3) emit_vec(std::integral_constant<int, 3>{});
+                    else if (a.qw == 4) emit_vec(std::integral_constant<int, 4>{});
+                    else emit_vec(std::integral_constant<int, 0>{});
+                } else {
+                    for (int e = threadIdx.x; e < words; e += blockDim.x) {
+                        uint32_t acc = 0;
+                        int sidx = s0;
+                        for (int ri = 0; ri < nr; ++ri) {
+                            const uint32_t* sl = ring + sidx * rs + e;
+                            for (int c = 0; c < a.qw; ++c) acc += sl[c * a.nbins];
+                            if (++sidx == ns) sidx = 0;
+                        }
+                        out[e] = acc;
+                    }
+                }
+            }
+        }
+    }
+}
+
 int gcd_int(int a, int b) {
     while (b) {
         const int t = a % b;
@@ -229,18 +449,102 @@ int gcd_int(int a, int b) {
 
 }  // namespace
 
+bool window_direct(const WindowGeom& g) { return g.wh == g.sh && g.ww == g.sw; }
+
+namespace {
+// The fused pass for images up to max_W wide: ring row words (rs), window
+// rows per group (G) and ring rows (nslots); rs = 0 when the pass does not
+// apply (stride = size, a column stride that does not divide the width, or
+// rows of cells too wide for shared memory).  Groups take as many window
+// rows as keep the ring within kFusedGroupWords (up to kFusedMaxGroup); rows
+// of windows with gaps between them (row stride above the height) are not
+// grouped.
+struct FusedPlan {
+    uint64_t rs = 0;
+    int group = 1, nslots = 1;
+};
+
+FusedPlan fused_plan(int max_W, const WindowGeom& g) {
+    FusedPlan p;
+    if (window_direct(g) || g.ww % g.sw != 0) return p;
+    const int ch = gcd_int(g.wh, g.sh), qh = g.wh / ch, qw = g.ww / g.sw, ph = g.sh / ch;
+    const int ncc = (max_W + g.sw - 1) / g.sw;
+    const uint64_t rs = ((uint64_t)(ncc > qw ? ncc : qw) * (uint64_t)g.nbins + 3u) & ~(uint64_t)3u;
+    if ((uint64_t)qh * rs > (uint64_t)kFusedSmemWords) return p;
+    p.rs = rs;
+    p.nslots = qh;
+    if (ph <= qh)
+        for (int G = 2; G <= kFusedMaxGroup; ++G) {
+            const int ns = (G - 1) * ph + qh;
+            if ((uint64_t)ns * rs > (uint64_t)kFusedGroupWords) break;
+            p.group = G;
+            p.nslots = ns;
+        }
+    return p;
+}
+}  // namespace
+
 uint64_t window_cell_words(int H, int W, const WindowGeom& g) {
+    if (window_direct(g) || fused_plan(W, g).rs) return 0;
     const int ch = gcd_int(g.wh, g.sh), cw = gcd_int(g.ww, g.sw);
     return (uint64_t)((H + ch - 1) / ch) * (uint64_t)((W + cw - 1) / cw) * (uint64_t)g.nbins;
 }
-
-bool window_direct(const WindowGeom& g) { return g.wh == g.sh && g.ww == g.sw; }
 
 cudaError_t launch_windows(const ldp_image_desc* d_descs, const ldp_image_desc* one, int count, int max_H,
                            int max_W, const WindowGeom& g, uint32_t* hist, uint32_t* cells,
                            uint64_t cell_stride, cudaStream_t s) {
     const int ch = gcd_int(g.wh, g.sh), cw = gcd_int(g.ww, g.sw);
     const bool direct = window_direct(g);
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int* status = status_word();
+    if (!status) return cudaErrorInvalidSymbol;
+    if (const FusedPlan fp = fused_plan(max_W, g); fp.rs) {
+        cudaError_t e = cudaFuncSetAttribute(k_window_fused, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)((kFusedSmemWords + 4) * sizeof(uint32_t)));
+        if (e != cudaSuccess) return e;
+        FusedArgs fa{};
+        fa.descs = d_descs;
+        if (one) fa.one = *one;
+        fa.ch = ch;
+        fa.cw = cw;
+        fa.qh = g.wh / ch;
+        fa.qw = g.ww / cw;
+        fa.ph = g.sh / ch;
+        fa.wh = g.wh;
+        fa.ww = g.ww;
+        fa.sh = g.sh;
+        fa.sw = g.sw;
+        fa.nbins = g.nbins;
+        fa.k = g.compact ? g.k : 0;
+        fa.row_stride = (int)fp.rs;
+        fa.group = fp.group;
+        fa.nslots = fp.nslots;
+        fa.hist = hist;
+        fa.max_H = max_H;
+        fa.max_W = max_W;
+        fa.status = status;
+        const size_t smem = sizeof(uint32_t) * ((size_t)fp.rs * (size_t)fp.nslots + 4);
+        int occ = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_window_fused, kFusedThreads, smem);
+        if (e != cudaSuccess) return e;
+        if (occ < 1) occ = 1;
+        // bands of window rows: enough work items for two waves of the GPU,
+        // each band at least one group long
+        const int nwr_max = (max_H <= g.wh) ? 1 : (max_H - g.wh + g.sh - 1) / g.sh + 1;
+        const int64_t want = 2LL * sms * occ;
+        int bands = (int)((want + count - 1) / count);
+        const int max_bands = (nwr_max + fp.group - 1) / fp.group;
+        if (bands > max_bands) bands = max_bands;
+        if (bands < 1) bands = 1;
+        fa.rows_per_band = (nwr_max + bands - 1) / bands;
+        fa.bands = (nwr_max + fa.rows_per_band - 1) / fa.rows_per_band;
+        const uint64_t items = (uint64_t)count * (uint64_t)fa.bands;
+        const unsigned grid = (unsigned)(items < (1u << 20) ? items : (1u << 20));
+        k_window_fused<<<grid, kFusedThreads, smem, s>>>(fa, count);
+        return cudaGetLastError();
+    }
     CellArgs ca{};
     ca.descs = d_descs;
     if (one) ca.one = *one;
@@ -255,10 +559,10 @@ cudaError_t launch_windows(const ldp_image_desc* d_descs, const ldp_image_desc* 
     ca.hist = hist;
     ca.cells = cells;
     ca.cell_stride = cell_stride;
+    ca.max_H = max_H;
+    ca.max_W = max_W;
+    ca.status = status;
     const int ncr = (max_H + ch - 1) / ch;
-    int dev = 0, sms = 1;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const uint64_t image_words = (uint64_t)ncr * (uint64_t)ncc_max * (uint64_t)g.nbins;
     if (image_words <= (uint64_t)kCellSmemWords) {
         // every cell of an image fits: one CTA per image
@@ -291,6 +595,9 @@ cudaError_t launch_windows(const ldp_image_desc* d_descs, const ldp_image_desc* 
     sa.cells = cells;
     sa.cell_stride = cell_stride;
     sa.hist = hist;
+    sa.max_H = max_H;
+    sa.max_W = max_W;
+    sa.status = status;
     const int nwr_max = (max_H <= g.wh) ? 1 : (max_H - g.wh + g.sh - 1) / g.sh + 1;
     const uint64_t items = (uint64_t)count * (uint64_t)nwr_max;
     k_window_sum<<<(unsigned)(items < (1u << 20) ? items : (1u << 20)), 256, 0, s>>>(sa, count, nwr_max);
@@ -329,7 +636,7 @@ uint64_t align256(uint64_t b) { return (b + 255u) & ~(uint64_t)255u; }
 uint64_t window_scratch(int H, int W, int k, const ldp_window_spec& ws, bool codes_given) {
     const ldp::WindowGeom g = window_geom(ws, k);
     uint64_t b = codes_given ? 0 : align256((uint64_t)(H - 2) * (uint64_t)(W - 2));
-    if (!ldp::window_direct(g)) b += ldp::window_cell_words(H, W, g) * sizeof(uint32_t);
+    b += ldp::window_cell_words(H, W, g) * sizeof(uint32_t);
     return b;
 }
 
@@ -391,7 +698,6 @@ uint64_t ldp_batch_window_scratch_bytes(int count, int max_H, int max_W, int k, 
         ws.sw < 1 || (ws.compact && k < 1))
         return 0;
     const ldp::WindowGeom g = window_geom(ws, k);
-    if (ldp::window_direct(g)) return 0;
     return (uint64_t)count * ldp::window_cell_words(max_H, max_W, g) * sizeof(uint32_t);
 }
 
@@ -408,7 +714,7 @@ int ldp_batch_window_hist(const ldp_image_desc* d_descs, int count, int max_H, i
     if (!d_hist) return ldp::report_error(LDP_EINVAL, "histogram pointer is NULL");
     ldp::Range range("ldp.batch_window_hist");
     const ldp::WindowGeom g = window_geom(ws, k);
-    const uint64_t words = ldp::window_direct(g) ? 0 : ldp::window_cell_words(max_H, max_W, g);
+    const uint64_t words = ldp::window_cell_words(max_H, max_W, g);
     if (words && (!d_scratch || scratch_bytes < (uint64_t)count * words * sizeof(uint32_t)))
         return ldp::report_error(LDP_EINVAL, "scratch missing or too small");
     cudaError_t e = ldp::launch_windows(d_descs, nullptr, count, max_H, max_W, g, d_hist,

@@ -116,15 +116,26 @@ def test_window_host_logic_without_gpu(lib):
                 assert lib.ldp_window_count(n, w, s) == oracle.window_count(n, w, s)
     assert lib.ldp_window_count(10, 0, 1) == -1 and lib.ldp_window_count(10, 3, 0) == -1
     ws = _abi.WindowSpec(20, 20, 10, 10, 1)
-    # overlapping windows: code map + cells of gcd(20, 10) = 10 pixels
-    cells = 49 * 64 * 56 * 4
-    assert lib.ldp_window_scratch_bytes(490, 640, 3, ws, 0) == ((488 * 638 + 255) // 256) * 256 + cells
-    assert lib.ldp_window_scratch_bytes(490, 640, 3, ws, 1) == cells
+    code_map = ((488 * 638 + 255) // 256) * 256
+    # overlapping windows whose column stride divides the width: one fused
+    # pass with the cells in shared memory, scratch for the code map only
+    assert lib.ldp_window_scratch_bytes(490, 640, 3, ws, 0) == code_map
+    assert lib.ldp_window_scratch_bytes(490, 640, 3, ws, 1) == 0
+    assert lib.ldp_batch_window_scratch_bytes(8, 490, 640, 0, _abi.WindowSpec(20, 20, 10, 10, 0)) == 0
+    # a column stride that does not divide the width: cells of gcd(20, 15) = 5
+    # pixels go through device scratch
+    ws15 = _abi.WindowSpec(20, 20, 15, 15, 1)
+    cells = 98 * 128 * 56 * 4
+    assert lib.ldp_window_scratch_bytes(490, 640, 3, ws15, 0) == code_map + cells
+    assert lib.ldp_window_scratch_bytes(490, 640, 3, ws15, 1) == cells
+    assert lib.ldp_batch_window_scratch_bytes(8, 490, 640, 0, _abi.WindowSpec(20, 20, 15, 15, 0)) == \
+        8 * 98 * 128 * 256 * 4
+    # rows of cells too wide for shared memory (1-pixel cells, 256 bins): scratch again
+    ws1 = _abi.WindowSpec(4, 4, 1, 1, 0)
+    assert lib.ldp_window_scratch_bytes(490, 640, 0, ws1, 1) == 490 * 640 * 256 * 4
     # stride = size: the cells are the windows, no cell scratch
     assert lib.ldp_window_scratch_bytes(490, 640, 3, _abi.WindowSpec(20, 20, 20, 20, 1), 1) == 0
     assert lib.ldp_window_scratch_bytes(490, 640, 0, _abi.WindowSpec(20, 20, 20, 20, 1), 1) == 0  # bad spec
-    assert lib.ldp_batch_window_scratch_bytes(8, 490, 640, 0, _abi.WindowSpec(20, 20, 10, 10, 0)) == \
-        8 * 49 * 64 * 256 * 4
     fake = ctypes.c_void_p(0x1000)
     assert lib.ldp_window_hist(fake, 10, 10, 10, 3, _abi.WindowSpec(0, 4, 4, 4, 1), fake, None, 0, None, 0,
                                None) == EINVAL
@@ -136,7 +147,7 @@ def test_window_host_logic_without_gpu(lib):
     assert lib.lbp_window_hist(fake, 10, 10, 10, _abi.WindowSpec(4, 4, 4, 4, 1), fake, fake, 8, None, 0,
                                None) == EINVAL
     assert lib.ldp_batch_window_hist(None, 1, 10, 10, 3, ws, fake, None, 0, None) == EINVAL
-    assert lib.ldp_batch_window_hist(fake, 1, 10, 10, 3, ws, fake, None, 0, None) == EINVAL  # no scratch
+    assert lib.ldp_batch_window_hist(fake, 1, 10, 10, 3, ws15, fake, None, 0, None) == EINVAL  # no scratch
 
 
 def test_code_mode_arguments_without_gpu(lib):

@@ -1,6 +1,8 @@
 """GPU parity of the sliding-window histograms (Sec. 3.2): cell histograms of
 gcd(size, stride) cells summed into windows, against the CPU oracle bit for
-bit, single images and batches."""
+bit, single images and batches.  The cases cover the three routes: stride =
+size (cells are the windows), the fused pass (column stride dividing the
+width: cell rows in shared memory), and cells through device scratch."""
 import numpy as np
 import pytest
 
@@ -34,12 +36,16 @@ def _h(t):
     (64, 90, (100, 200), (7, 9)),     # one window larger than the image
     (3, 3, (1, 1), (1, 1)),           # one interior pixel, 1-pixel windows
     (33, 517, (6, 35), (4, 21)),      # ragged cells, gcd 2 x 7
+    (61, 203, (8, 16), (24, 8)),      # fused: gaps between window rows, columns overlap
+    (40, 300, (30, 6), (10, 2)),      # fused: three cell rows and three cells per window
+    (700, 900, (20, 20), (10, 10)),   # fused: bands of window rows per CTA
+    (57, 1030, (4, 9), (2, 3)),       # fused: 344 cells per ring row
 ])
 def test_single_image_windows(env, H, W, window, stride):
     torch, ldp, oracle, synth = env
     img = synth.image(H * 7 + W, H, W, 3.0)
     d = torch.from_numpy(img).cuda()
-    for k, compact in ((3, True), (1, True), (6, False)):
+    for k, compact in ((3, True), (1, True), (4, True), (6, False)):
         h, c = ldp.window_hist(d, k=k, window=window, stride=stride, compact=compact)
         torch.cuda.synchronize()
         h_ref, c_ref = oracle.extract_windows(img, k=k, window=window, stride=stride, compact=compact)
@@ -76,10 +82,12 @@ def test_ties_and_flat_images(env):
             assert np.array_equal(_h(h), oracle.extract_windows(img, k=k, window=(12, 10), stride=(4, 5))[0])
 
 
-@pytest.mark.parametrize("window,stride", [((20, 20), None), ((24, 16), (12, 8))])
-def test_batch_windows_from_plan_codes(env, window, stride):
+@pytest.mark.parametrize("window,stride,gap", [((20, 20), None, 0), ((24, 16), (12, 8), 0),
+                                               ((24, 16), (12, 8), 1), ((20, 20), (15, 15), 0)])
+def test_batch_windows_from_plan_codes(env, window, stride, gap):
     """Code maps of an uneven batch from one persistent launch (codes only),
-    then the windows of every image in one call."""
+    then the windows of every image in one call (gap = 1: histogram offsets
+    that are not multiples of four words)."""
     torch, ldp, oracle, synth = env
     seeds = np.arange(900, 941)
     sizes = [synth.sizes(int(s), 3, 260) for s in seeds]
@@ -93,13 +101,13 @@ def test_batch_windows_from_plan_codes(env, window, stride):
     d_img = torch.from_numpy(host).cuda()
     d_codes = torch.zeros(lay.code_bytes, dtype=torch.uint8, device="cuda")
     descs = lay.descs(d_img.data_ptr(), d_codes.data_ptr())
-    offs = np.concatenate([[0], np.cumsum(np.array(nwin) * 56)[:-1]]).astype(np.uint64)
+    offs = np.concatenate([[0], np.cumsum(np.array(nwin) * 56 + gap)[:-1]]).astype(np.uint64) + gap
     descs["hist_offset"] = offs
     d_desc = torch.from_numpy(descs.view(np.uint8)).cuda()
     d_count = torch.tensor([lay.n], dtype=torch.int32, device="cuda")
     with ldp.BatchPlan(lay.n, lay.pixels, k=k, regions=(1, 1)) as plan:
         plan.run(d_desc, d_count, None)
-    d_hist = torch.full((int(sum(nwin)) * 56,), -1, dtype=torch.int32, device="cuda")
+    d_hist = torch.full((int(sum(nwin)) * 56 + gap * (lay.n + 1),), -1, dtype=torch.int32, device="cuda")
     ldp.batch_window_hist(d_desc, lay.n, (max(Hs), max(Ws)), k, window, stride, hist=d_hist)
     torch.cuda.synchronize()
     hist = _h(d_hist)
@@ -108,3 +116,41 @@ def test_batch_windows_from_plan_codes(env, window, stride):
         ref, _ = oracle.extract_windows(img, k=k, window=window, stride=stride)
         o = int(offs[i])
         assert np.array_equal(hist[o:o + ref.size].reshape(ref.shape), ref), (i, Hs[i], Ws[i])
+    if gap:  # the words between the images' histograms are untouched
+        for i in range(lay.n):
+            assert int(d_hist[int(offs[i]) - 1]) == -1
+
+
+@pytest.mark.parametrize("window,stride", [((20, 20), (10, 10)), ((20, 20), (15, 15)), ((10, 10), None)])
+def test_batch_windows_reject_images_past_the_bounds(env, window, stride):
+    """An image larger than max_H x max_W is skipped on every route (fused,
+    cells through scratch, stride = size): its histogram words are left as
+    they were and the device status word reports a bad descriptor; the
+    other images are exact."""
+    torch, ldp, oracle, synth = env
+    Hs, Ws = [60, 90, 60], [80, 70, 130]  # image 2 is wider than max_W = 100
+    lay = ldp.BatchLayout.build(Hs, Ws, hist_len=0)
+    host = np.zeros(lay.img_bytes, dtype=np.uint8)
+    synth.batch_into(host, np.arange(3) + 50, Hs, Ws, lay.pitches, lay.img_off)
+    d_img = torch.from_numpy(host).cuda()
+    d_codes = torch.zeros(lay.code_bytes, dtype=torch.uint8, device="cuda")
+    descs = lay.descs(d_img.data_ptr(), d_codes.data_ptr())
+    sh, sw = window if stride is None else stride
+    nwin = [ldp.window_count(h, window[0], sh) * ldp.window_count(w, window[1], sw) for h, w in zip(Hs, Ws)]
+    offs = np.concatenate([[0], np.cumsum(np.array(nwin) * 56)[:-1]]).astype(np.uint64)
+    descs["hist_offset"] = offs
+    d_desc = torch.from_numpy(descs.view(np.uint8)).cuda()
+    d_count = torch.tensor([3], dtype=torch.int32, device="cuda")
+    with ldp.BatchPlan(3, lay.pixels, k=3, regions=(1, 1)) as plan:
+        plan.run(d_desc, d_count, None)
+    ldp.device_status()  # clear
+    d_hist = torch.full((int(sum(nwin)) * 56,), -1, dtype=torch.int32, device="cuda")
+    ldp.batch_window_hist(d_desc, 3, (100, 100), 3, window, stride, hist=d_hist)
+    torch.cuda.synchronize()
+    assert ldp.device_status() & 1
+    hist = _h(d_hist)
+    for i in range(2):
+        ref, _ = oracle.extract_windows(np.ascontiguousarray(lay.image(host, i)), k=3, window=window, stride=stride)
+        assert np.array_equal(hist[int(offs[i]):int(offs[i]) + ref.size].reshape(ref.shape), ref), i
+    assert (d_hist[int(offs[2]):].cpu().numpy() == -1).all()
+    assert ldp.device_status() == 0
