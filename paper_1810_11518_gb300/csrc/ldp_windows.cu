@@ -33,7 +33,7 @@ namespace ldp {
 namespace {
 
 constexpr int kCellThreads = 256;
-constexpr int kCellSmemWords = 12160;  // counters at most: with the 512-byte table, 48 KB of shared memory
+constexpr int kCellSmemWords = 12156;  // counters at most: with 4 junk words and the 512-byte table, 48 KB
 
 struct CellArgs {
     const ldp_image_desc* descs;  // nullptr: the single image `one`
@@ -47,6 +47,7 @@ struct CellArgs {
     uint64_t cell_stride;
     int max_H, max_W;  // bounds of the images' sizes
     int* status;       // device status word
+    int junk;          // shared word past the counters: columns past the image, codes without a bin
 };
 
 __device__ __forceinline__ ldp_image_desc desc_of(const CellArgs& a, int i) {
@@ -76,7 +77,7 @@ __device__ __forceinline__ int cell_of(int y, int cw, float inv_cw) {
 // the row is 4-byte aligned), blocks of 128 columns at a time; the four
 // columns' cells are found once per block and reused for every row.
 __global__ void __launch_bounds__(kCellThreads) k_cell_hist(CellArgs a, int count, int ncr_max) {
-    extern __shared__ uint32_t cnt[];  // a.chunk * a.nbins counters (sized at launch)
+    extern __shared__ uint32_t cnt[];  // a.chunk * a.nbins counters (sized at launch), then the junk word
     __shared__ int16_t lut[256];
     for (int c = threadIdx.x; c < 256; c += blockDim.x)
         lut[c] = (a.k >= 1) ? __ldg(&g_bin_table.bin[a.k][c]) : (int16_t)c;
@@ -125,7 +126,7 @@ __global__ void __launch_bounds__(kCellThreads) k_cell_hist(CellArgs a, int coun
 #pragma unroll
                 for (int t = 0; t < 4; ++t) {
                     const int b = lut[(w4 >> (8 * t)) & 0xFFu];
-                    if (in[t] && b >= 0) atomicAdd(&cnt[off[t] + b], 1u);
+                    atomicAdd(&cnt[(in[t] && b >= 0) ? off[t] + b : a.junk], 1u);
                 }
             }
         }
@@ -141,7 +142,7 @@ __global__ void __launch_bounds__(kCellThreads) k_cell_hist(CellArgs a, int coun
 // warps over rows, lanes over four consecutive columns whose cells are found
 // once for all rows.
 __global__ void __launch_bounds__(kCellThreads) k_cell_hist_image(CellArgs a, int count) {
-    extern __shared__ uint32_t cnt[];  // ncr * ncc * nbins counters of the largest image
+    extern __shared__ uint32_t cnt[];  // ncr * ncc * nbins counters of the largest image, then the junk word
     __shared__ int16_t lut[256];
     for (int c = threadIdx.x; c < 256; c += blockDim.x)
         lut[c] = (a.k >= 1) ? __ldg(&g_bin_table.bin[a.k][c]) : (int16_t)c;
@@ -182,7 +183,7 @@ __global__ void __launch_bounds__(kCellThreads) k_cell_hist_image(CellArgs a, in
 #pragma unroll
                 for (int t = 0; t < 4; ++t) {
                     const int b = lut[(w4 >> (8 * t)) & 0xFFu];
-                    if (in[t] && b >= 0) atomicAdd(&cnt[rbase + off[t] + b], 1u);
+                    atomicAdd(&cnt[(in[t] && b >= 0) ? rbase + off[t] + b : a.junk], 1u);
                 }
             }
         }
@@ -567,14 +568,15 @@ cudaError_t launch_windows(const ldp_image_desc* d_descs, const ldp_image_desc* 
     if (image_words <= (uint64_t)kCellSmemWords) {
         // every cell of an image fits: one CTA per image
         const unsigned grid = (unsigned)(count < sms * 16 ? count : sms * 16);
-        k_cell_hist_image<<<grid, kCellThreads, sizeof(uint32_t) * (size_t)image_words, s>>>(ca, count);
+        ca.junk = (int)image_words;
+        k_cell_hist_image<<<grid, kCellThreads, sizeof(uint32_t) * ((size_t)image_words + 4), s>>>(ca, count);
     } else {
         // CTAs loop over (image, cell row) items: a few waves of the GPU
         const uint64_t pairs = (uint64_t)count * (uint64_t)ncr;
         const uint64_t cap = (uint64_t)sms * 32;
         dim3 grid((unsigned)(pairs < cap ? pairs : cap), (ncc_max + ca.chunk - 1) / ca.chunk);
-        k_cell_hist<<<grid, kCellThreads, sizeof(uint32_t) * (size_t)ca.chunk * (size_t)g.nbins, s>>>(ca, count,
-                                                                                                    ncr);
+        ca.junk = ca.chunk * g.nbins;
+        k_cell_hist<<<grid, kCellThreads, sizeof(uint32_t) * ((size_t)ca.junk + 4), s>>>(ca, count, ncr);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || direct) return e;
