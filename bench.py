@@ -83,14 +83,41 @@ TRAFFIC_SOURCES = ("paper_1810_11518_gb300/csrc/ldp_device.cuh", "paper_1810_115
 TRAFFIC_SHA256 = "815e12e83717dc219d3386188adced54c3020a23bbd9a8a13f21a75b77ed4f13"
 
 
-def measured_traffic(pixels, k, H, W):
-    if (k, H, W) != (3, 490, 640):
-        return None
+# Warp-instruction issue slots x 32 per input pixel of the same kernel, from
+# the same capture (smsp__inst_executed = 280,581,607 for 512 x 640x490).
+ISSUE_SLOTS_PER_PX = 280581607 * 32 / (512 * 640 * 490)
+
+
+def sources_match():
     h = hashlib.sha256()
     for f in TRAFFIC_SOURCES:
         with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
-    return int(round(TRAFFIC_PER_PX * pixels)) if h.hexdigest() == TRAFFIC_SHA256 else None
+    return h.hexdigest() == TRAFFIC_SHA256
+
+
+def measured_traffic(pixels, k, H, W):
+    if (k, H, W) != (3, 490, 640):
+        return None
+    return int(round(TRAFFIC_PER_PX * pixels)) if sources_match() else None
+
+
+def issue_roofline(pixels, k, H, W, kernel_ms, sms, sm_mhz):
+    """The roof that binds the persistent kernel: instruction issue.  Peak =
+    SMs x 4 schedulers x 32 lanes x the SM clock sampled in the timed region
+    (one warp instruction per scheduler and cycle); achieved = the captured
+    issue slots per pixel x pixels / kernel time.  None when the kernel
+    sources differ from the captured ones or the workload is another."""
+    if (k, H, W) != (3, 490, 640) or not sources_match() or not sm_mhz:
+        return None
+    achieved = ISSUE_SLOTS_PER_PX * pixels / (kernel_ms * 1e-3) / 1e12
+    peak = sms * 4 * 32 * sm_mhz * 1e6 / 1e12
+    return {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3),
+            "unit": "T thread-instruction slots/s", "frac": round(achieved / peak, 4),
+            "slots_per_pixel": round(ISSUE_SLOTS_PER_PX, 2),
+            "source": "ncu smsp__inst_executed of these kernel sources (512 x 640x490 capture); "
+                      f"peak = {sms} SMs x 4 schedulers x 32 lanes x {sm_mhz:.0f} MHz (median SM clock in the "
+                      "timed region)"}
 
 
 def algorithmic_bytes(Hs, Ws, hist_len):
@@ -667,6 +694,9 @@ def main():
                          "kernel_ms": round(k_ms, 4), "algorithmic_bytes_per_launch": alg_bytes,
                          "peak_source": f"{peak_src} hbm_gbs",
                          "binding_roof": "integer pipes and issue (ALU 73%, issue 81% in ncu); see profiles/"},
+            "issue_roofline": issue_roofline(n * H * W, k, H, W, k_ms,
+                                             torch.cuda.get_device_properties(dev).multi_processor_count,
+                                             (clk or {}).get("sm_mhz")),
             "e2e": e2e,
             "gpu_launches": 3 * a.steps,
             "clocks": clk,
