@@ -7,10 +7,13 @@
 // arithmetic, and
 //     out = (wy0 (wx0 p00 + wx1 p01) + wy1 (wx0 p10 + wx1 p11) + 2^21) >> 22
 // (at most 2048 * 2048 * 255 + 2^21 < 2^32).  A CTA owns kRows output rows of
-// one image: the rows' coordinates and source row addresses are computed once
-// into shared memory, each thread owns output columns (coalesced stores) and
-// computes their coordinates once for all kRows rows, in 32-bit arithmetic
-// whenever the numbers fit.
+// one image: the rows' coordinates and source row addresses, and (for output
+// widths up to kMaxCols) every column's coordinate, are computed once into
+// shared memory, in 32-bit arithmetic whenever the numbers fit.  Threads then
+// take groups of four output columns of the rows in turn (the CTA's work
+// spread evenly whatever the width), gather the sixteen source bytes and
+// store the four results as one 32-bit word where the destination allows.
+// Wider outputs compute their column coordinates per thread instead.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -21,8 +24,9 @@ namespace ldp {
 
 namespace {
 
-constexpr int kRows = 32;
+constexpr int kRows = 64;
 constexpr int kThreads = 256;
+constexpr int kMaxCols = 4096;     // output widths whose column table fits in shared memory
 constexpr int kStatusBadCrop = 8;  // device status bit: a crop descriptor was rejected
 
 __device__ __forceinline__ void coord(int i, int n_src, int n_dst, int& i0, int& w1) {
@@ -84,7 +88,9 @@ __global__ void __launch_bounds__(kThreads) k_resize(ResizeArgs a) {
     __shared__ const uint8_t* s_pa[kRows];
     __shared__ const uint8_t* s_pb[kRows];
     __shared__ uint32_t s_wy1[kRows];
+    __shared__ uint32_t s_col[kMaxCols];  // x0 << 12 | wx1 of each output column (OW <= kMaxCols)
     const int r0 = blockIdx.x * kRows;
+    const bool table = a.OW <= kMaxCols;
     for (int img = blockIdx.y; img < a.count; img += gridDim.y) {
         const ldp_crop_desc d = a.descs ? a.descs[img] : a.one;
         const bool ok = d.src && d.dst && d.ch >= 1 && d.cw >= 1 && d.cy >= 0 && d.cx >= 0 &&
@@ -93,7 +99,7 @@ __global__ void __launch_bounds__(kThreads) k_resize(ResizeArgs a) {
             if (threadIdx.x == 0 && blockIdx.x == 0) atomicOr(a.status, kStatusBadCrop);
             continue;
         }
-        __syncthreads();  // the previous image's row table is no longer read
+        __syncthreads();  // the previous image's tables are no longer read
         if (threadIdx.x < kRows && r0 + (int)threadIdx.x < a.OH) {
             int y0, w;
             coord(r0 + threadIdx.x, d.ch, a.OH, y0, w);
@@ -102,23 +108,74 @@ __global__ void __launch_bounds__(kThreads) k_resize(ResizeArgs a) {
             s_pb[threadIdx.x] = d.src + (size_t)(d.cy + y1) * (size_t)d.pitch + d.cx;
             s_wy1[threadIdx.x] = (uint32_t)w;
         }
+        if (table)
+            for (int j = threadIdx.x; j < a.OW; j += blockDim.x) {
+                int x0, wx1;
+                coord(j, d.cw, a.OW, x0, wx1);
+                s_col[j] = ((uint32_t)x0 << 12) | (uint32_t)wx1;  // x0 < 2^20, wx1 <= 2047
+            }
         __syncthreads();
         const int nr = min(kRows, a.OH - r0);
         uint8_t* drow = d.dst + (size_t)r0 * (size_t)d.dst_pitch;
-        for (int j = threadIdx.x; j < a.OW; j += blockDim.x) {
-            int x0, wx1;
-            coord(j, d.cw, a.OW, x0, wx1);
-            const int xb = x0 + 1 < d.cw ? x0 + 1 : x0;
-            const uint32_t wx0 = 2048u - (uint32_t)wx1;
-            uint8_t* dp = drow + j;
-            for (int r = 0; r < nr; ++r, dp += d.dst_pitch) {
+        if (table) {
+            // bilinear value of output column j from source rows pa / pb
+            auto pixel = [&](const uint8_t* pa, const uint8_t* pb, uint32_t wy1, int j) -> uint32_t {
+                const uint32_t c = s_col[j];
+                const int x0 = (int)(c >> 12);
+                const uint32_t wx1 = c & 0xFFFu, wx0 = 2048u - wx1;
+                const int xb = x0 + 1 < d.cw ? x0 + 1 : x0;
+                const uint32_t top = wx0 * __ldg(pa + x0) + wx1 * __ldg(pa + xb);
+                const uint32_t bot = wx0 * __ldg(pb + x0) + wx1 * __ldg(pb + xb);
+                return ((2048u - wy1) * top + wy1 * bot + (1u << 21)) >> 22;
+            };
+            const int ncg = (a.OW + 3) / 4;  // groups of four columns
+            const bool words = (((uintptr_t)d.dst | (uintptr_t)d.dst_pitch) & 3u) == 0;
+            // items (row, group) = threadIdx.x + k * blockDim.x, stepped without a division
+            const int dr = (int)blockDim.x / ncg, dc = (int)blockDim.x % ncg;
+            int r = (int)threadIdx.x / ncg, cg = (int)threadIdx.x % ncg;
+            for (; r < nr;) {
                 const uint8_t* pa = s_pa[r];
                 const uint8_t* pb = s_pb[r];
-                const uint32_t top = wx0 * __ldg(pa + x0) + (uint32_t)wx1 * __ldg(pa + xb);
-                const uint32_t bot = wx0 * __ldg(pb + x0) + (uint32_t)wx1 * __ldg(pb + xb);
                 const uint32_t wy1 = s_wy1[r];
-                const uint32_t v = (2048u - wy1) * top + wy1 * bot;
-                *dp = (uint8_t)((v + (1u << 21)) >> 22);
+                const int j0 = 4 * cg;
+                uint8_t* dp = drow + (size_t)r * (size_t)d.dst_pitch + j0;
+                if (j0 + 4 <= a.OW) {
+                    const uint32_t v0 = pixel(pa, pb, wy1, j0), v1 = pixel(pa, pb, wy1, j0 + 1);
+                    const uint32_t v2 = pixel(pa, pb, wy1, j0 + 2), v3 = pixel(pa, pb, wy1, j0 + 3);
+                    if (words) {
+                        *reinterpret_cast<uint32_t*>(dp) = v0 | (v1 << 8) | (v2 << 16) | (v3 << 24);
+                    } else {
+                        dp[0] = (uint8_t)v0;
+                        dp[1] = (uint8_t)v1;
+                        dp[2] = (uint8_t)v2;
+                        dp[3] = (uint8_t)v3;
+                    }
+                } else {
+                    for (int j = j0; j < a.OW; ++j) dp[j - j0] = (uint8_t)pixel(pa, pb, wy1, j);
+                }
+                cg += dc;
+                r += dr;
+                if (cg >= ncg) {
+                    cg -= ncg;
+                    ++r;
+                }
+            }
+        } else {
+            for (int j = threadIdx.x; j < a.OW; j += blockDim.x) {
+                int x0, wx1;
+                coord(j, d.cw, a.OW, x0, wx1);
+                const int xb = x0 + 1 < d.cw ? x0 + 1 : x0;
+                const uint32_t wx0 = 2048u - (uint32_t)wx1;
+                uint8_t* dp = drow + j;
+                for (int rr = 0; rr < nr; ++rr, dp += d.dst_pitch) {
+                    const uint8_t* pa = s_pa[rr];
+                    const uint8_t* pb = s_pb[rr];
+                    const uint32_t top = wx0 * __ldg(pa + x0) + (uint32_t)wx1 * __ldg(pa + xb);
+                    const uint32_t bot = wx0 * __ldg(pb + x0) + (uint32_t)wx1 * __ldg(pb + xb);
+                    const uint32_t wy1 = s_wy1[rr];
+                    const uint32_t v = (2048u - wy1) * top + wy1 * bot;
+                    *dp = (uint8_t)((v + (1u << 21)) >> 22);
+                }
             }
         }
     }

@@ -280,12 +280,15 @@ struct FusedArgs {
 __global__ void __launch_bounds__(kFusedThreads, 2) k_window_fused(FusedArgs a, int count) {
     extern __shared__ uint4 ring4[];  // nslots x row_stride counters, then 4 junk words
     uint32_t* ring = reinterpret_cast<uint32_t*>(ring4);
-    __shared__ int16_t lut[256];
-    for (int c = threadIdx.x; c < 256; c += blockDim.x)
-        lut[c] = (a.k >= 1) ? __ldg(&g_bin_table.bin[a.k][c]) : (int16_t)c;
+    __shared__ int lut4[256];  // 4 x the bin of each code, -1 for codes without a bin
+    for (int c = threadIdx.x; c < 256; c += blockDim.x) {
+        const int b = (a.k >= 1) ? (int)__ldg(&g_bin_table.bin[a.k][c]) : c;
+        lut4[c] = b >= 0 ? 4 * b : -1;
+    }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const float inv_cw = 1.0f / (float)a.cw, inv_ch = 1.0f / (float)a.ch;
     const int rs = a.row_stride, ns = a.nslots;
+    const uint32_t ring_addr = (uint32_t)__cvta_generic_to_shared(ring);
     // one word past the ring takes the counts of columns past the image and of
     // codes without a bin, so the count needs no branch
     const uint32_t junk_addr = (uint32_t)__cvta_generic_to_shared(ring + ns * rs);
@@ -307,30 +310,38 @@ __global__ void __launch_bounds__(kFusedThreads, 2) k_window_fused(FusedArgs a, 
         const bool single = ncb <= nwarps;
         const int rpw = single ? nwarps / ncb : 1;
 
-        auto block_cells = [&](int cb, int(&off)[4], bool(&in)[4]) {
+        // the lane's four columns of block cb: byte offsets of their cells
+        // within a ring row (4 * cell * nbins) and which lie inside
+        auto block_cells = [&](int cb, uint32_t(&off4)[4], bool(&in)[4]) {
             const int yq = 1 + cb * 128 + 4 * lane;  // columns yq .. yq+3
 #pragma unroll
             for (int t = 0; t < 4; ++t) {
                 in[t] = yq + t < W - 1;
-                off[t] = in[t] ? cell_of(yq + t, a.cw, inv_cw) * a.nbins : 0;
+                off4[t] = in[t] ? 4u * (uint32_t)(cell_of(yq + t, a.cw, inv_cw) * a.nbins) : 0u;
             }
         };
         // image rows x0, x0 + step, ... < x1 of column block cb, each into the
         // ring row of its cell row (cell rows n0 .. n0 + nslots - 1; n0 in
-        // ring row s_n0)
-        auto count_rows = [&](int cb, const int(&off)[4], const bool(&in)[4], int x0, int x1, int step, int n0,
-                              int s_n0) {
+        // ring row s_n0), four rows' loads in flight.  A row whose 128 codes
+        // all have a bin and lie inside counts without a test per pixel.
+        auto count_rows = [&](int cb, const uint32_t(&off4)[4], const bool(&in)[4], int x0, int x1, int step,
+                              int n0, int s_n0) {
             const int yq = 1 + cb * 128 + 4 * lane;
             const bool v4 = al && in[3];
-            const uint8_t* base = d.codes + (yq - 1);
-            for (int x = x0; x < x1; x += 4 * step) {
+            const size_t pstep = (size_t)step * (size_t)d.code_pitch;
+            const uint8_t* p = d.codes + (size_t)(x0 - 1) * (size_t)d.code_pitch + (yq - 1);
+            int cr = cell_of(x0, a.ch, inv_ch);  // cell row of the current image row, ending before nb
+            int sl = s_n0 + (cr - n0);
+            if (sl >= ns) sl -= ns;
+            uint32_t sbase = ring_addr + 4u * (uint32_t)(sl * rs);
+            int nb = (cr + 1) * a.ch;
+            for (int x = x0; x < x1; x += 4 * step, p += 4 * pstep) {
                 uint32_t w[4];
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    const int xx = x + j * step;
-                    const uint8_t* cp = base + (size_t)(xx - 1) * (size_t)d.code_pitch;
+                    const uint8_t* cp = p + j * pstep;
                     w[j] = 0;
-                    if (xx < x1) {
+                    if (x + j * step < x1) {
                         if (v4) {
                             w[j] = __ldg(reinterpret_cast<const unsigned int*>(cp));
                         } else {
@@ -344,22 +355,34 @@ __global__ void __launch_bounds__(kFusedThreads, 2) k_window_fused(FusedArgs a, 
                 for (int j = 0; j < 4; ++j) {
                     const int xx = x + j * step;
                     if (xx < x1) {
-                        int sl = s_n0 + (cell_of(xx, a.ch, inv_ch) - n0);
-                        if (sl >= ns) sl -= ns;
-                        uint32_t* slot = ring + sl * rs;
-                        const uint32_t slot_addr = (uint32_t)__cvta_generic_to_shared(slot);
+                        while (xx >= nb) {  // into the next cell row
+                            nb += a.ch;
+                            if (++sl == ns) sl = 0;
+                            sbase = ring_addr + 4u * (uint32_t)(sl * rs);
+                        }
+                        int b4[4];
 #pragma unroll
-                        for (int t = 0; t < 4; ++t) {
-                            const int b = lut[(w[j] >> (8 * t)) & 0xFFu];
-                            const uint32_t addr =
-                                (in[t] && b >= 0) ? slot_addr + 4u * (uint32_t)(off[t] + b) : junk_addr;
-                            asm volatile("red.shared.add.u32 [%0], 1;" ::"r"(addr) : "memory");
+                        for (int t = 0; t < 4; ++t) b4[t] = lut4[(w[j] >> (8 * t)) & 0xFFu];
+                        const bool ok = in[3] && (b4[0] | b4[1] | b4[2] | b4[3]) >= 0;
+                        if (__all_sync(0xffffffffu, ok)) {
+#pragma unroll
+                            for (int t = 0; t < 4; ++t) {
+                                const uint32_t addr = sbase + off4[t] + (uint32_t)b4[t];
+                                asm volatile("red.shared.add.u32 [%0], 1;" ::"r"(addr) : "memory");
+                            }
+                        } else {
+#pragma unroll
+                            for (int t = 0; t < 4; ++t) {
+                                const uint32_t addr =
+                                    (in[t] && b4[t] >= 0) ? sbase + off4[t] + (uint32_t)b4[t] : junk_addr;
+                                asm volatile("red.shared.add.u32 [%0], 1;" ::"r"(addr) : "memory");
+                            }
                         }
                     }
                 }
             }
         };
-        int my_off[4] = {0, 0, 0, 0};
+        uint32_t my_off[4] = {0u, 0u, 0u, 0u};
         bool my_in[4] = {false, false, false, false};
         const int my_cb = warp % ncb, my_phase = warp / ncb;
         if (single) block_cells(my_cb, my_off, my_in);
@@ -383,7 +406,7 @@ __global__ void __launch_bounds__(kFusedThreads, 2) k_window_fused(FusedArgs a, 
                     if (my_phase < rpw) count_rows(my_cb, my_off, my_in, x0 + my_phase, x1, rpw, n0, s_n0);
                 } else {
                     for (int cb = warp; cb < ncb; cb += nwarps) {
-                        int off[4];
+                        uint32_t off[4];
                         bool in[4];
                         block_cells(cb, off, in);
                         count_rows(cb, off, in, x0, x1, 1, n0, s_n0);

@@ -30,6 +30,8 @@ def env():
     ((120, 160), (119, 159, 1, 1), (7, 5)),     # one source pixel
     ((50, 700), (3, 10, 44, 600), (333, 17)),   # extreme aspect change
     ((1, 1), None, (4, 300)),
+    ((6, 9), None, (3, 4101)),                  # wider than the column table
+    ((300, 200), (0, 0, 300, 199), (130, 4096)),  # widest output with the table
 ])
 def test_resize_parity(env, shape, crop, out_hw):
     torch, ldp, oracle, synth = env
