@@ -40,6 +40,8 @@ def _h(t):
     (40, 300, (30, 6), (10, 2)),      # fused: three cell rows and three cells per window
     (700, 900, (20, 20), (10, 10)),   # fused: bands of window rows per CTA
     (57, 1030, (4, 9), (2, 3)),       # fused: 344 cells per ring row
+    (50, 60, (80, 80), (40, 40)),     # fused: one window, larger than the image
+    (30, 30, (64, 64), (16, 16)),     # fused: a window wider than the image's cells (zero cells past it)
 ])
 def test_single_image_windows(env, H, W, window, stride):
     torch, ldp, oracle, synth = env
