@@ -63,6 +63,30 @@ def _img(img):
     return ctypes.c_void_p(img.data_ptr()), int(H), int(W), int(img.stride(0))
 
 
+def _cuda(t, name, dtype=None, min_numel=None, contiguous=False):
+    """A caller's device buffer, checked before its address reaches a kernel."""
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must be a {dtype} tensor")
+    if contiguous and not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if min_numel is not None and t.numel() < min_numel:
+        raise ValueError(f"{name} holds {t.numel()} elements, at least {min_numel} are needed")
+    return t
+
+
+def _host(t, name, dtype, min_numel):
+    """A caller's host buffer (pinned for overlapped copies), checked likewise."""
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous {dtype} host tensor")
+    if t.numel() < min_numel:
+        raise ValueError(f"{name} holds {t.numel()} elements, at least {min_numel} are needed")
+    return t
+
+
 def _alloc_codes(img, H, W, out):
     torch = _torch()
     if out is not None:
@@ -116,8 +140,8 @@ def region_hist(img, k: int = 3, regions=(1, 1), compact: bool = True, with_code
     nb = comb(8, k) if compact else 256
     if hist is None:
         hist = torch.empty((R, C, nb), dtype=torch.int32, device=img.device)
-    elif hist.numel() != R * C * nb or not hist.is_contiguous():
-        raise ValueError("hist must be a contiguous tensor of R*C*nbins int32")
+    else:
+        _cuda(hist, "hist", torch.int32, R * C * nb, contiguous=True)
     cptr, pc, out = None, 0, None
     if with_codes:
         out, pc = _alloc_codes(img, H, W, codes_out)
@@ -146,6 +170,8 @@ def lbp_region_hist(img, regions=(1, 1), with_codes: bool = True, hist=None, cod
     R, C = regions
     if hist is None:
         hist = torch.empty((R, C, 256), dtype=torch.int32, device=img.device)
+    else:
+        _cuda(hist, "hist", torch.int32, R * C * 256, contiguous=True)
     cptr, pc, out = None, 0, None
     if with_codes:
         out, pc = _alloc_codes(img, H, W, codes_out)
@@ -172,8 +198,8 @@ def _window_run(fn, img, k, window, stride, compact, with_codes, hist, codes_out
     shape = (window_count(H, wh, sh), window_count(W, ww, sw), nb)
     if hist is None:
         hist = torch.empty(shape, dtype=torch.int32, device=img.device)
-    elif hist.numel() != shape[0] * shape[1] * nb or not hist.is_contiguous():
-        raise ValueError(f"hist must be a contiguous int32 tensor of {shape[0] * shape[1] * nb} elements")
+    else:
+        _cuda(hist, "hist", torch.int32, shape[0] * shape[1] * nb, contiguous=True)
     cptr, pc, out = None, 0, None
     if with_codes:
         out, pc = _alloc_codes(img, H, W, codes_out)
@@ -209,8 +235,11 @@ def batch_window_hist(d_descs, count: int, max_hw, k: int, window, stride=None, 
                       hist=None, stream=None):
     """Window histograms of `count` code maps already in device memory (descriptors
     `d_descs`, a CUDA tensor of DESC_DTYPE records; windows of image i at
-    hist + hist_offset).  k = 0: raw 256 bins (LBP maps)."""
+    hist + hist_offset, hist a CUDA int32 tensor covering every offset).
+    k = 0: raw 256 bins (LBP maps)."""
     torch = _torch()
+    _cuda(d_descs, "d_descs", min_numel=count * DESC_DTYPE.itemsize // d_descs.element_size())
+    _cuda(hist, "hist", torch.int32)
     wh, ww = window
     sh, sw = (wh, ww) if stride is None else stride
     ws = WindowSpec(wh, ww, sh, sw, int(compact))
@@ -233,8 +262,9 @@ def resize(img, out_hw=(260, 260), crop=None, out=None, stream=None):
     OH, OW = out_hw
     if out is None:
         out = torch.empty((OH, OW), dtype=torch.uint8, device=img.device)
-    elif out.dtype != torch.uint8 or out.dim() != 2 or tuple(out.shape) != (OH, OW) or out.stride(1) != 1:
-        raise ValueError(f"out must be a uint8 tensor of shape {(OH, OW)} with unit column stride")
+    elif (not out.is_cuda or out.dtype != torch.uint8 or out.dim() != 2 or tuple(out.shape) != (OH, OW)
+          or out.stride(1) != 1):
+        raise ValueError(f"out must be a uint8 CUDA tensor of shape {(OH, OW)} with unit column stride")
     _abi.call("ldp_resize", p, H, W, P, cy, cx, ch, cw, ctypes.c_void_p(out.data_ptr()), OH, OW,
               int(out.stride(0)), _stream(stream))
     return out
@@ -243,6 +273,7 @@ def resize(img, out_hw=(260, 260), crop=None, out=None, stream=None):
 def batch_resize(d_descs, count: int, out_hw=(260, 260), stream=None) -> None:
     """Every crop of `d_descs` (a CUDA tensor of CROP_DTYPE records) resized to out_hw in one launch;
     rejected descriptors are skipped and reported by device_status() (bit 3)."""
+    _cuda(d_descs, "d_descs", min_numel=count * CROP_DTYPE.itemsize // d_descs.element_size())
     _abi.call("ldp_batch_resize", ctypes.c_void_p(d_descs.data_ptr()), int(count), int(out_hw[0]),
               int(out_hw[1]), _stream(stream))
 
@@ -266,8 +297,8 @@ def hist_distance(q, g, metric: int = DIST_CHI2, out=None, stream=None):
     dt = torch.float32 if metric == DIST_CHI2 else torch.int64
     if out is None:
         out = torch.empty((nq, ng), dtype=dt, device=q.device)
-    elif out.dtype != dt or tuple(out.shape) != (nq, ng) or out.stride(1) != 1:
-        raise ValueError(f"out must be a {dt} tensor of shape {(nq, ng)} with unit column stride")
+    elif not out.is_cuda or out.dtype != dt or tuple(out.shape) != (nq, ng) or out.stride(1) != 1:
+        raise ValueError(f"out must be a {dt} CUDA tensor of shape {(nq, ng)} with unit column stride")
     _abi.call("ldp_hist_distance", ctypes.c_void_p(q.data_ptr()), nq, int(q.stride(0)),
               ctypes.c_void_p(g.data_ptr()), ng, int(g.stride(0)), D, int(metric),
               ctypes.c_void_p(out.data_ptr()), int(out.stride(0)), _stream(stream))
@@ -308,8 +339,11 @@ class Pipeline:
                 np.ascontiguousarray(layout.pitches, dtype=np.int32),
                 np.ascontiguousarray(layout.code_off, dtype=np.int64),
                 np.ascontiguousarray(layout.code_pitches, dtype=np.int32)]
-        if h_hist.numel() < layout.n * self.hist_len:
-            raise ValueError("h_hist is smaller than n x hist_len")
+        torch = _torch()
+        _host(h_img, "h_img", torch.uint8, layout.img_bytes)
+        _host(h_hist, "h_hist", torch.int32, layout.n * self.hist_len)
+        if h_codes is not None:
+            _host(h_codes, "h_codes", torch.uint8, layout.code_bytes)
         cptr = ctypes.c_void_p(h_codes.data_ptr()) if h_codes is not None else None
         _abi.call("ldp_pipeline_run", self._h, layout.n, ctypes.c_void_p(h_img.data_ptr()),
                   *[ctypes.c_void_p(a.ctypes.data) for a in arrs[:4]], cptr,
@@ -358,6 +392,9 @@ def batch_run_noalloc(d_descs, count: int, max_pixels: int, max_side: int, d_his
     2^21 ints shared by all calls; see ldp_batch_run_noalloc in ldp.h).
     For callers that budget device memory once and cannot allocate per batch.
     Calls must not overlap on the GPU."""
+    _cuda(d_descs, "d_descs", min_numel=count * DESC_DTYPE.itemsize // d_descs.element_size())
+    if d_hist is not None:
+        _cuda(d_hist, "d_hist", _torch().int32)
     hist_ptr = ctypes.c_void_p(d_hist.data_ptr()) if d_hist is not None else None
     _abi.call("ldp_batch_run_noalloc", ctypes.c_void_p(d_descs.data_ptr()), int(count), int(max_pixels),
               int(max_side), int(k), RegionSpec(regions[0], regions[1], int(compact)), hist_ptr, _stream(stream))
@@ -450,6 +487,10 @@ class BatchPlan:
         """d_descs: device buffer of DESC_DTYPE records; d_count: device int32
         holding the image count; d_hist: device int32 buffer (or None)."""
         fn = "lbp_batch_run" if self.lbp else "ldp_batch_run"
+        _cuda(d_descs, "d_descs")
+        _cuda(d_count, "d_count", _torch().int32, 1)
+        if d_hist is not None:
+            _cuda(d_hist, "d_hist", _torch().int32)
         hist_ptr = ctypes.c_void_p(d_hist.data_ptr()) if d_hist is not None else None
         _abi.call(fn, self._h, ctypes.c_void_p(d_descs.data_ptr()), ctypes.c_void_p(d_count.data_ptr()),
                   hist_ptr, _stream(stream))
