@@ -241,9 +241,9 @@ __global__ void __launch_bounds__(256) k_window_sum(SumArgs a, int count, int nw
     }
 }
 
-constexpr int kFusedThreads = 512;
+constexpr int kFusedThreads = 256;
 constexpr int kFusedSmemWords = 40960;    // ring counters at most (160 KB)
-constexpr int kFusedGroupWords = 16384;   // ring size up to which window rows are grouped (64 KB)
+constexpr int kFusedGroupWords = 12288;   // ring size up to which window rows are grouped (48 KB)
 constexpr int kFusedMaxGroup = 8;         // window rows per group at most
 
 struct FusedArgs {
@@ -271,13 +271,14 @@ struct FusedArgs {
 // the image stay out), then every output word e = b*nbins + bin of each of
 // the G window rows is the sum over the window row's cell rows of the ring
 // words e + c*nbins, c < qw (window b covers cells b .. b+qw-1 of the row;
-// cells past the image are zero).  Three barriers per group.  Each warp
-// counts one column block of 128 columns (a lane's four consecutive
-// columns, their cells found once per image) on every rpw-th image row of
-// the group, four rows' loads in flight; wider images loop over blocks.
+// cells past the image are zero).  Three barriers per group.  The group's
+// (128-column block, image row) tasks are split into equal runs of
+// consecutive tasks, one per warp (a lane takes four consecutive columns,
+// their cells found once per block), four rows' loads in flight; small CTAs
+// (eight warps, four per SM) keep the barriers' idle time short.
 // Counts are shared-memory reductions without a branch (a column past the
 // image or a code without a bin counts into a junk word past the ring).
-__global__ void __launch_bounds__(kFusedThreads, 2) k_window_fused(FusedArgs a, int count) {
+__global__ void __launch_bounds__(kFusedThreads, 4) k_window_fused(FusedArgs a, int count) {
     extern __shared__ uint4 ring4[];  // nslots x row_stride counters, then 4 junk words
     uint32_t* ring = reinterpret_cast<uint32_t*>(ring4);
     __shared__ int lut4[256];  // 4 x the bin of each code, -1 for codes without a bin
@@ -307,8 +308,6 @@ __global__ void __launch_bounds__(kFusedThreads, 2) k_window_fused(FusedArgs a, 
         const bool vec = (a.nbins & 3) == 0 && ((reinterpret_cast<uintptr_t>(out_img) & 15u) == 0);
         const bool al = ((reinterpret_cast<uintptr_t>(d.codes) | (uintptr_t)d.code_pitch) & 3u) == 0;
         const int ncb = (W - 2 + 127) / 128;
-        const bool single = ncb <= nwarps;
-        const int rpw = single ? nwarps / ncb : 1;
 
         // the lane's four columns of block cb: byte offsets of their cells
         // within a ring row (4 * cell * nbins) and which lie inside
@@ -382,10 +381,6 @@ __global__ void __launch_bounds__(kFusedThreads, 2) k_window_fused(FusedArgs a, 
                 }
             }
         };
-        uint32_t my_off[4] = {0u, 0u, 0u, 0u};
-        bool my_in[4] = {false, false, false, false};
-        const int my_cb = warp % ncb, my_phase = warp / ncb;
-        if (single) block_cells(my_cb, my_off, my_in);
 
         int next = a0 * a.ph;  // first cell row not in the ring
         for (int g0 = a0; g0 < a1; g0 += a.group) {
@@ -399,17 +394,22 @@ __global__ void __launch_bounds__(kFusedThreads, 2) k_window_fused(FusedArgs a, 
             }
             __syncthreads();
             if (n0 < n1) {
-                // image rows of cell rows [n0, n1) that hold codes
+                // image rows of cell rows [n0, n1) that hold codes; tasks
+                // (column block, row) in block-major order, an equal share of
+                // consecutive tasks per warp (one or two blocks each)
                 const int x0 = max(n0 * a.ch, 1), x1 = min(n1 * a.ch, H - 1);
                 const int s_n0 = n0 % ns;
-                if (single) {
-                    if (my_phase < rpw) count_rows(my_cb, my_off, my_in, x0 + my_phase, x1, rpw, n0, s_n0);
-                } else {
-                    for (int cb = warp; cb < ncb; cb += nwarps) {
+                const int R = x1 - x0;
+                if (R > 0) {
+                    const int T = R * ncb;
+                    const int t1 = (int)((int64_t)T * (warp + 1) / nwarps);
+                    for (int t = (int)((int64_t)T * warp / nwarps); t < t1;) {
+                        const int cb = t / R, r0 = t - cb * R, r1 = min(R, r0 + (t1 - t));
                         uint32_t off[4];
                         bool in[4];
                         block_cells(cb, off, in);
-                        count_rows(cb, off, in, x0, x1, 1, n0, s_n0);
+                        count_rows(cb, off, in, x0 + r0, x0 + r1, 1, n0, s_n0);
+                        t += r1 - r0;
                     }
                 }
             }
