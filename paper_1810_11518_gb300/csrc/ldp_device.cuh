@@ -343,9 +343,9 @@ constexpr int kStatusWaitTimeout = 4;  // device status bit: a bounded wait gave
 constexpr int kStatusBounds = 16;      // checked builds: an index outside its buffer was skipped
 
 // Checked builds (-DLDP_CHECKED) test every shared- and global-memory index
-// of the tile loop against its buffer; a violation sets kStatusBounds in the
-// device status word and the access is skipped (nothing traps).  In normal
-// builds the test is compiled away.
+// of the tile loop (and of the window and resize kernels) against its buffer;
+// a violation sets kStatusBounds in the device status word and the access is
+// skipped (nothing traps).  In normal builds the test is compiled away.
 __device__ __forceinline__ bool index_ok(bool ok, int* status) {
 #ifdef LDP_CHECKED
     if (!ok) atomicOr(status, kStatusBounds);

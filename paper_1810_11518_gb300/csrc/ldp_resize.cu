@@ -18,6 +18,7 @@
 
 #include <cstdint>
 
+#include "ldp_device.cuh"
 #include "ldp_launch.h"
 
 namespace ldp {
@@ -124,6 +125,7 @@ __global__ void __launch_bounds__(kThreads) k_resize(ResizeArgs a) {
                 const int x0 = (int)(c >> 12);
                 const uint32_t wx1 = c & 0xFFFu, wx0 = 2048u - wx1;
                 const int xb = x0 + 1 < d.cw ? x0 + 1 : x0;
+                if (!index_ok(j < kMaxCols && x0 < d.cw, a.status)) return 0u;
                 const uint32_t top = wx0 * __ldg(pa + x0) + wx1 * __ldg(pa + xb);
                 const uint32_t bot = wx0 * __ldg(pb + x0) + wx1 * __ldg(pb + xb);
                 return ((2048u - wy1) * top + wy1 * bot + (1u << 21)) >> 22;

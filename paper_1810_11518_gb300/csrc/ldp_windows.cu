@@ -126,7 +126,8 @@ __global__ void __launch_bounds__(kCellThreads) k_cell_hist(CellArgs a, int coun
 #pragma unroll
                 for (int t = 0; t < 4; ++t) {
                     const int b = lut[(w4 >> (8 * t)) & 0xFFu];
-                    atomicAdd(&cnt[(in[t] && b >= 0) ? off[t] + b : a.junk], 1u);
+                    const int ix = (in[t] && b >= 0) ? off[t] + b : a.junk;
+                    if (index_ok(ix <= a.junk, a.status)) atomicAdd(&cnt[ix], 1u);
                 }
             }
         }
@@ -183,7 +184,8 @@ __global__ void __launch_bounds__(kCellThreads) k_cell_hist_image(CellArgs a, in
 #pragma unroll
                 for (int t = 0; t < 4; ++t) {
                     const int b = lut[(w4 >> (8 * t)) & 0xFFu];
-                    atomicAdd(&cnt[(in[t] && b >= 0) ? rbase + off[t] + b : a.junk], 1u);
+                    const int ix = (in[t] && b >= 0) ? rbase + off[t] + b : a.junk;
+                    if (index_ok(ix <= a.junk, a.status)) atomicAdd(&cnt[ix], 1u);
                 }
             }
         }
@@ -233,7 +235,11 @@ __global__ void __launch_bounds__(256) k_window_sum(SumArgs a, int count, int nw
                 uint32_t s = 0;
                 for (int ci = i0; ci < i1; ++ci) {
                     const uint32_t* row = cells + ((size_t)ci * (size_t)ncc) * (size_t)a.nbins + bin;
-                    for (int cj = j0; cj < j1; ++cj) s += __ldg(row + (size_t)cj * (size_t)a.nbins);
+                    for (int cj = j0; cj < j1; ++cj)
+                        if (index_ok(((uint64_t)ci * (uint64_t)ncc + (uint64_t)cj) * (uint64_t)a.nbins + (uint64_t)bin <
+                                         a.cell_stride,
+                                     a.status))
+                            s += __ldg(row + (size_t)cj * (size_t)a.nbins);
                 }
                 out[(size_t)wb * (size_t)a.nbins + bin] = s;
             }
@@ -293,6 +299,7 @@ __global__ void __launch_bounds__(kFusedThreads, 4) k_window_fused(FusedArgs a, 
     // one word past the ring takes the counts of columns past the image and of
     // codes without a bin, so the count needs no branch
     const uint32_t junk_addr = (uint32_t)__cvta_generic_to_shared(ring + ns * rs);
+    const uint32_t ring_bytes = 4u * (uint32_t)(ns * rs + 4);  // ring and junk words (checked builds)
     const uint64_t items = (uint64_t)count * (uint64_t)a.bands;
     for (uint64_t it = blockIdx.x; it < items; it += gridDim.x) {
         const int img = (int)(it / (uint64_t)a.bands), band = (int)(it % (uint64_t)a.bands);
@@ -367,14 +374,16 @@ __global__ void __launch_bounds__(kFusedThreads, 4) k_window_fused(FusedArgs a, 
 #pragma unroll
                             for (int t = 0; t < 4; ++t) {
                                 const uint32_t addr = sbase + off4[t] + (uint32_t)b4[t];
-                                asm volatile("red.shared.add.u32 [%0], 1;" ::"r"(addr) : "memory");
+                                if (index_ok(addr - ring_addr < ring_bytes, a.status))
+                                    asm volatile("red.shared.add.u32 [%0], 1;" ::"r"(addr) : "memory");
                             }
                         } else {
 #pragma unroll
                             for (int t = 0; t < 4; ++t) {
                                 const uint32_t addr =
                                     (in[t] && b4[t] >= 0) ? sbase + off4[t] + (uint32_t)b4[t] : junk_addr;
-                                asm volatile("red.shared.add.u32 [%0], 1;" ::"r"(addr) : "memory");
+                                if (index_ok(addr - ring_addr < ring_bytes, a.status))
+                                    asm volatile("red.shared.add.u32 [%0], 1;" ::"r"(addr) : "memory");
                             }
                         }
                     }
@@ -425,10 +434,11 @@ __global__ void __launch_bounds__(kFusedThreads, 4) k_window_fused(FusedArgs a, 
                         uint4 acc = make_uint4(0, 0, 0, 0);
                         int sidx = s0;
                         for (int ri = 0; ri < nr; ++ri) {
-                            const uint32_t* sl = ring + sidx * rs + e;
 #pragma unroll
                             for (int c = 0; c < (QW ? QW : a.qw); ++c) {
-                                const uint4 v = *reinterpret_cast<const uint4*>(sl + c * a.nbins);
+                                const int ix = sidx * rs + e + c * a.nbins;
+                                if (!index_ok(ix + 3 < ns * rs, a.status)) continue;
+                                const uint4 v = *reinterpret_cast<const uint4*>(ring + ix);
                                 acc.x += v.x;
                                 acc.y += v.y;
                                 acc.z += v.z;
@@ -451,7 +461,8 @@ __global__ void __launch_bounds__(kFusedThreads, 4) k_window_fused(FusedArgs a, 
                         int sidx = s0;
                         for (int ri = 0; ri < nr; ++ri) {
                             const uint32_t* sl = ring + sidx * rs + e;
-                            for (int c = 0; c < a.qw; ++c) acc += sl[c * a.nbins];
+                            for (int c = 0; c < a.qw; ++c)
+                                if (index_ok(sidx * rs + e + c * a.nbins < ns * rs, a.status)) acc += sl[c * a.nbins];
                             if (++sidx == ns) sidx = 0;
                         }
                         out[e] = acc;

@@ -1,6 +1,7 @@
 """The checked build (-DLDP_CHECKED: every shared- and global-memory index of
-the tile loop tested against its buffer, violations recorded in the device
-status word instead of trapping) runs the parity cases with no violation.
+the tile loop, the window kernels and the resize gathers tested against its
+buffer, violations recorded in the device status word instead of trapping)
+runs the parity cases with no violation.
 It stands in for a memory checker, which this environment does not offer.
 The cases run in a child process that loads the checked library."""
 import os
@@ -54,6 +55,33 @@ for v in range(ldp.num_variants()):
     for i in range(lay.n):
         h_ref, _ = oracle.extract(np.ascontiguousarray(lay.image(host, i)), k=3, R=7, C=6)
         assert np.array_equal(hist[i * lay.hist_len:(i + 1) * lay.hist_len].reshape(h_ref.shape), h_ref), (v, i)
+# sliding windows on every route (fused ring, stride = size, cells through scratch), single and batched
+img = synth.image(5, 77, 150, 3.0)
+d = torch.from_numpy(img).cuda()
+for window, stride in (((20, 16), (10, 8)), ((12, 10), (4, 5)), ((20, 20), None), ((9, 12), (15, 20)),
+                       ((64, 64), (16, 16))):
+    for k, compact in ((3, True), (4, True), (6, False)):
+        h, _ = ldp.window_hist(d, k=k, window=window, stride=stride, compact=compact, with_codes=False)
+        h_ref, _ = oracle.extract_windows(img, k=k, window=window, stride=stride, compact=compact)
+        assert np.array_equal(h.cpu().numpy().astype(np.uint32), h_ref), (window, stride, k)
+    descs = lay.descs(d_img.data_ptr(), d_codes.data_ptr())
+    sh, sw = window if stride is None else stride
+    nwin = [ldp.window_count(h_, window[0], sh) * ldp.window_count(w_, window[1], sw) for h_, w_ in zip(Hs, Ws)]
+    offs = np.concatenate([[0], np.cumsum(np.array(nwin) * 56)[:-1]]).astype(np.uint64)
+    descs["hist_offset"] = offs
+    wd = torch.from_numpy(descs.view(np.uint8)).cuda()
+    wh = torch.zeros(int(sum(nwin)) * 56, dtype=torch.int32, device="cuda")
+    ldp.batch_window_hist(wd, lay.n, (max(Hs), max(Ws)), 3, window, stride, hist=wh)
+    wh = wh.cpu().numpy().astype(np.uint32)
+    for i in range(0, lay.n, 7):
+        ref, _ = oracle.extract_windows(np.ascontiguousarray(lay.image(host, i)), k=3, window=window, stride=stride)
+        assert np.array_equal(wh[int(offs[i]):int(offs[i]) + ref.size].reshape(ref.shape), ref), (window, i)
+# crop-and-resize, both column paths
+for shape, crop, out_hw in (((490, 640), (100, 180, 300, 280), (260, 260)), ((9, 23), None, (9, 46)),
+                            ((6, 9), None, (3, 4101))):
+    src = synth.image(shape[0] + shape[1], shape[0], shape[1], 3.0)
+    got = ldp.resize(torch.from_numpy(src).cuda(), out_hw, crop=crop)
+    assert np.array_equal(got.cpu().numpy(), oracle.resize(src, out_hw, crop=crop)), shape
 torch.cuda.synchronize()
 print("status", ldp.device_status())
 """
