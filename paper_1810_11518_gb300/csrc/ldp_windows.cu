@@ -133,8 +133,10 @@ __global__ void __launch_bounds__(kCellThreads) k_cell_hist(CellArgs a, int coun
         }
         __syncthreads();
         uint32_t* out = a.direct ? a.hist + d.hist_offset : a.cells + (uint64_t)img * a.cell_stride;
-        out += ((size_t)i * (size_t)ncc + (size_t)j0) * (size_t)a.nbins;
-        for (int e = threadIdx.x; e < words; e += blockDim.x) out[e] = cnt[e];
+        const uint64_t first = ((uint64_t)i * (uint64_t)ncc + (uint64_t)j0) * (uint64_t)a.nbins;
+        out += first;
+        if (a.direct || index_ok(first + (uint64_t)words <= a.cell_stride, a.status))
+            for (int e = threadIdx.x; e < words; e += blockDim.x) out[e] = cnt[e];
     }
 }
 
@@ -191,7 +193,8 @@ __global__ void __launch_bounds__(kCellThreads) k_cell_hist_image(CellArgs a, in
         }
         __syncthreads();
         uint32_t* out = a.direct ? a.hist + d.hist_offset : a.cells + (uint64_t)img * a.cell_stride;
-        for (int e = threadIdx.x; e < words; e += blockDim.x) out[e] = cnt[e];
+        if (a.direct || index_ok((uint64_t)words <= a.cell_stride, a.status))
+            for (int e = threadIdx.x; e < words; e += blockDim.x) out[e] = cnt[e];
     }
 }
 
@@ -699,8 +702,11 @@ int run_windows(int mode, const uint8_t* d_img, int H, int W, int pitch, int k, 
     if ((rc = ldp::run_plain(mode, d_img, H, W, pitch, k < 1 ? 1 : k, 1, 1, 0, nullptr, d_codes, code_pitch, stream)))
         return rc;
     ldp_image_desc one{d_img, H, W, pitch, code_pitch, d_codes, 0};
-    cudaError_t e = ldp::launch_windows(nullptr, &one, 1, H, W, window_geom(ws, k), d_hist,
-                                        reinterpret_cast<uint32_t*>(sp), 0, static_cast<cudaStream_t>(stream));
+    const ldp::WindowGeom g = window_geom(ws, k);
+    // one image: the cell stride is the image's own cell words (the bound a
+    // checked build tests the cell reads against)
+    cudaError_t e = ldp::launch_windows(nullptr, &one, 1, H, W, g, d_hist, reinterpret_cast<uint32_t*>(sp),
+                                        ldp::window_cell_words(H, W, g), static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return ldp::report_cuda(e, "window kernels");
     return LDP_OK;
 }
