@@ -332,6 +332,11 @@ __device__ __forceinline__ int bin_of(int code, const HistCfg& hc, int k) {
 }
 
 constexpr int kWarpSlots = 6;  // region slots a warp tile may touch and still count in smem
+// shared 256-bin slots of a warp's histogram: LBP adds a junk slot that takes
+// the counts of columns past the interior (LBP produces every code, so no
+// bin of a counted slot is free for them)
+template <int MODE>
+__host__ __device__ constexpr int warp_hist_slots() { return is_ldp(MODE) ? kWarpSlots : kWarpSlots + 1; }
 
 // Staged input (bulk-copy engine): per warp a ring of kStages stages of
 // kStageRows image rows, kRowBytes bytes each (the 130 bytes a 128-column
@@ -417,7 +422,7 @@ __device__ __forceinline__ int band_lo(int b, int n, int nb) {
 // zero on entry and on exit): the flush adds every non-zero bin to the global
 // histogram and resets it.  In the LDP modes bin 0 of a slot (code 0, which
 // they never produce) takes the counts of columns past the interior and is
-// never read.
+// never read; LBP has a junk slot for them.
 // Region grids too fine for kWarpSlots slots count straight into global
 // memory.  `ph` holds the ring's per-stage wait parities across tiles.
 template <int MODE, int K, int RW, bool HIST, bool STAGED>
@@ -475,14 +480,22 @@ __device__ __forceinline__ void warp_tile(const Job& jb, const HistCfg& hc, int 
     // shared-memory byte address of bin 0 of each column's current slot
     uint32_t sbase[4] = {0u, 0u, 0u, 0u};
     const uint32_t wh_addr = HIST && use_smem && is_ldp(MODE) ? smem_addr(wh) : 0u;
+    // LBP: word index of bin 0 of each column's current slot (the junk slot
+    // for columns past the interior)
+    int lbase[4] = {0, 0, 0, 0};
     auto set_sbase = [&]() {
 #pragma unroll
-        for (int t = 0; t < 4; ++t) sbase[t] = wh_addr + 4u * (uint32_t)(rowb + colb[t]);
+        for (int t = 0; t < 4; ++t) {
+            if constexpr (is_ldp(MODE))
+                sbase[t] = wh_addr + 4u * (uint32_t)(rowb + colb[t]);
+            else
+                lbase[t] = valid[t] ? rowb + colb[t] : kWarpSlots * 256;
+        }
     };
     if constexpr (HIST) {
         next_b = band_lo(ri + 1, H, hc.R);
         rowb = use_smem ? 0 : ri * hc.C;
-        if (use_smem && is_ldp(MODE)) set_sbase();
+        if (use_smem) set_sbase();
     }
 
     // codes of output row u (byte t of `packed` = column v+t) -> code map and histogram
@@ -502,7 +515,7 @@ __device__ __forceinline__ void warp_tile(const Job& jb, const HistCfg& hc, int 
                 ++ri;
                 next_b = band_lo(ri + 1, H, hc.R);
                 rowb = use_smem ? (ri - ri_lo) * ncs * 256 : ri * hc.C;
-                if (use_smem && is_ldp(MODE)) set_sbase();
+                if (use_smem) set_sbase();
             }
             if (use_smem && is_ldp(MODE)) {
                 // LDP codes spread over the bins: one byte extract, one
@@ -520,8 +533,8 @@ __device__ __forceinline__ void warp_tile(const Job& jb, const HistCfg& hc, int 
                 // 255); the compiler's shared atomicAdd is faster there
 #pragma unroll
                 for (int t = 0; t < 4; ++t) {
-                    const int idx = rowb + colb[t] + (int)((packed >> (8 * t)) & 0xFFu);
-                    if (valid[t] && index_ok(idx < kWarpSlots * 256, status)) atomicAdd(&wh[idx], 1u);
+                    const int idx = lbase[t] + (int)((packed >> (8 * t)) & 0xFFu);
+                    if (index_ok(idx < warp_hist_slots<MODE>() * 256, status)) atomicAdd(&wh[idx], 1u);
                 }
             } else {
 #pragma unroll

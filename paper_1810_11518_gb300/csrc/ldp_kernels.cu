@@ -50,16 +50,22 @@ __device__ __forceinline__ HistCfg to_hc(const HistArgs& h) {
     return c;
 }
 
-// Shared memory of a CTA: per warp a private kWarpSlots x 256-bin histogram
-// (with HIST) and a bulk-copy ring (staged variants).
-template <class V, bool HIST>
+// Shared memory of a CTA: per warp a private histogram of SLOTS x 256 bins
+// (with HIST) and, in the staged variants, a bulk-copy ring.
+template <class V, bool HIST, int SLOTS, bool ST = V::ST>
 struct WarpSmem {
-    uint32_t h[HIST ? V::NW : 1][HIST ? kWarpSlots * 256 : 1];
-    WarpRing ring[V::ST ? V::NW : 1];
+    uint32_t h[HIST ? V::NW : 1][HIST ? SLOTS * 256 : 1];
+    WarpRing ring[V::NW];
+};
+template <class V, bool HIST, int SLOTS>
+struct WarpSmem<V, HIST, SLOTS, false> {
+    uint32_t h[HIST ? V::NW : 1][HIST ? SLOTS * 256 : 1];
 };
 
-template <class V, bool HIST>
-__device__ __forceinline__ uint32_t* warp_setup(WarpSmem<V, HIST>& s, WarpRing** ring) {
+// The warp's ring (staged variants) and histogram, whose counted slots are
+// zeroed (a junk slot is never read).
+template <class V, bool HIST, int SLOTS>
+__device__ __forceinline__ uint32_t* warp_setup(WarpSmem<V, HIST, SLOTS>& s, WarpRing** ring) {
     const int w = threadIdx.x >> 5;
     *ring = nullptr;
     if constexpr (V::ST) {
@@ -76,14 +82,14 @@ __device__ __forceinline__ uint32_t* warp_setup(WarpSmem<V, HIST>& s, WarpRing**
 // ---------------- single image: one warp per tile ----------------
 template <int MODE, int K, class V, bool HIST>
 __global__ void __launch_bounds__(V::NW * 32, V::MB) k_plain(JobArgs ja, HistArgs ha) {
-    __shared__ WarpSmem<V, HIST> sh;
+    __shared__ WarpSmem<V, HIST, warp_hist_slots<MODE>()> sh;
     const Job jb = to_job(ja);
     const int ntx = (jb.W - 2 + kTileW - 1) / kTileW;
     const int nty = (jb.H - 2 + V::RPW - 1) / V::RPW;
     const int w = blockIdx.x * V::NW + (threadIdx.x >> 5);
     if (w >= ntx * nty) return;  // whole warp
     WarpRing* ring;
-    uint32_t* wh = warp_setup<V, HIST>(sh, &ring);
+    uint32_t* wh = warp_setup(sh, &ring);
     uint32_t ph = 0;
     warp_tile<MODE, K, V::RPW, HIST, V::ST>(jb, to_hc(ha), (w / ntx) * V::RPW, (w % ntx) * kTileW, wh, ring, ph,
                                             ja.status);
@@ -96,12 +102,12 @@ __global__ void __launch_bounds__(V::NW * 32, V::MB) k_plain(JobArgs ja, HistArg
 // barrier is ever needed.
 template <int MODE, int K, class V, bool HIST>
 __global__ void __launch_bounds__(V::NW * 32, V::MB) k_batch(BatchArgs a) {
-    __shared__ WarpSmem<V, HIST> sh;
+    __shared__ WarpSmem<V, HIST, warp_hist_slots<MODE>()> sh;
     const HistCfg hc = to_hc(a.hc);
     const int lane = threadIdx.x & 31;
     const int total = *a.scr.total;
     WarpRing* ring;
-    uint32_t* wh = warp_setup<V, HIST>(sh, &ring);
+    uint32_t* wh = warp_setup(sh, &ring);
     uint32_t ph = 0;
     for (;;) {
         int t = 0, img = 0;
