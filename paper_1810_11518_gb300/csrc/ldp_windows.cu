@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(kCellThreads) k_cell_hist(CellArgs a, int coun
 // Whole-image items, for images whose every cell fits in shared memory (the
 // face-sized crops): one CTA per image, counters zeroed and stored once,
 // warps over rows, lanes over four consecutive columns whose cells are found
-// once for all rows.
+// once for all rows (several rows per warp step in a narrow last block).
 __global__ void __launch_bounds__(kCellThreads) k_cell_hist_image(CellArgs a, int count) {
     extern __shared__ uint32_t cnt[];  // ncr * ncc * nbins counters of the largest image, then the junk word
     __shared__ int16_t lut[256];
@@ -162,7 +162,13 @@ __global__ void __launch_bounds__(kCellThreads) k_cell_hist_image(CellArgs a, in
         __syncthreads();
         const bool al = (((uintptr_t)d.codes | (uintptr_t)d.code_pitch) & 3u) == 0;
         for (int yb = 1; yb < W - 1; yb += 128) {
-            const int yq = yb + 4 * lane;  // columns yq .. yq+3 (code columns yq-1 .. yq+2)
+            // a block narrower than 128 columns (the image's last) takes
+            // several rows per warp step: lp lanes per row (a power of two
+            // covering its columns), 32 / lp rows at once
+            const int ng = (min(128, W - 1 - yb) + 3) / 4;  // four-column groups of the block
+            const int lp = ng > 16 ? 32 : ng > 8 ? 16 : ng > 4 ? 8 : ng > 2 ? 4 : ng > 1 ? 2 : 1;
+            const int rows = 32 / lp;
+            const int yq = yb + 4 * (lane % lp);  // columns yq .. yq+3 (code columns yq-1 .. yq+2)
             int off[4];
             bool in[4];
 #pragma unroll
@@ -172,7 +178,7 @@ __global__ void __launch_bounds__(kCellThreads) k_cell_hist_image(CellArgs a, in
             }
             const bool vec = al && in[3];  // yq - 1 is a multiple of 4
 #pragma unroll 4
-            for (int x = 1 + warp; x < H - 1; x += nwarps) {
+            for (int x = 1 + warp * rows + lane / lp; x < H - 1; x += nwarps * rows) {
                 const int rbase = cell_of(x, a.ch, inv_ch) * ncc * a.nbins;
                 const uint8_t* cp = d.codes + (size_t)(x - 1) * (size_t)d.code_pitch + (yq - 1);
                 uint32_t w4 = 0;
