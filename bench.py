@@ -78,9 +78,9 @@ def dist_env():
 # profiles/k_batch_ldp_k3_512img_full.md), scaled to a launch by its pixels.
 # Valid only for the kernel sources it was taken on: any change to them
 # reports traffic as null until a new capture is recorded here.
-TRAFFIC_PER_PX = 300.009e6 / (512 * 640 * 490)
+TRAFFIC_PER_PX = 299.414e6 / (512 * 640 * 490)
 TRAFFIC_SOURCES = ("paper_1810_11518_gb300/csrc/ldp_device.cuh", "paper_1810_11518_gb300/csrc/ldp_kernels.cu")
-TRAFFIC_SHA256 = "32986e37c86ddeb01950c02774e47b84cc022f4870cefba790bde47e397679cb"
+TRAFFIC_SHA256 = "0f4de6b006a1fd41dbca14e4671a5f81e7755c1ceee4520fc186060f20f5114d"
 
 
 # Warp-instruction issue slots x 32 per input pixel of the same kernel, from
@@ -344,6 +344,13 @@ def time_face_pipeline(ldp, torch, dev, lay, d_img, k, steps, seed=7):
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     t = np.zeros(3)
     with ldp.BatchPlan(n, faces.pixels, k=k, regions=(1, 1)) as plan:
+        from paper_1810_11518_gb300 import autotune
+
+        props = torch.cuda.get_device_properties(dev)
+        ent = autotune.lookup(torch.cuda.get_device_name(dev), props.multi_processor_count, "batch", k, "codes",
+                              faces.pixels / n)
+        if ent:
+            plan.set_config(ent["variant"], ent["ctas_per_sm"])
         for it in range(3 + steps):
             ev[0].record()
             ldp.batch_resize(d_crops, n, (OH, OW))
@@ -363,7 +370,8 @@ def time_face_pipeline(ldp, torch, dev, lay, d_img, k, steps, seed=7):
             "ms_per_step": round(ms, 4), "faces_per_s": round(n / (ms * 1e-3), 1),
             "value": round(faces.pixels / (ms * 1e-3) / 1e6, 3), "unit": "Mpixel/s of 260x260 faces",
             "stage_ms": {"resize": round(float(t[0]), 4), "ldp_codes": round(float(t[1]), 4),
-                         "windows": round(float(t[2]), 4)}}
+                         "windows": round(float(t[2]), 4)},
+            "codes_variant": ldp.variant_name(ent["variant"]) if ent else ldp.variant_name(0)}
 
 
 def time_distances(ldp, torch, dev, d_hist, n, hist_len, steps):

@@ -85,7 +85,7 @@ def store(key: str, entry: dict, path: str | None = None) -> None:
     os.replace(tmp, path)
 
 
-def _tune_workload(name, Hs, Ws, seeds, k, lbp, sigma, out):
+def _tune_workload(name, Hs, Ws, seeds, k, lbp, sigma, out, hist=True):
     import numpy as np
     import torch
 
@@ -104,9 +104,10 @@ def _tune_workload(name, Hs, Ws, seeds, k, lbp, sigma, out):
     d_count = torch.tensor([lay.n], dtype=torch.int32, device="cuda")
     dev = torch.cuda.get_device_properties(0)
     with ldp.BatchPlan(lay.n, lay.pixels, k=k, regions=(R, C), lbp=lbp) as plan:
-        res = tune_plan(plan, d_desc, d_count, d_hist)
-    key = make_key(torch.cuda.get_device_name(0), dev.multi_processor_count, "batch", k if not lbp else 0,
-                   "lbp+hist+codes" if lbp else "hist+codes", lay.pixels / lay.n)
+        res = tune_plan(plan, d_desc, d_count, d_hist if hist else None)
+    mode = ("lbp+" if lbp else "") + ("hist+codes" if hist else "codes")
+    key = make_key(torch.cuda.get_device_name(0), dev.multi_processor_count, "batch", k if not lbp else 0, mode,
+                   lay.pixels / lay.n)
     store(key, res, out)
     print(key, res["name"], res["ctas_per_sm"], f"{res['kernel_ms']:.4f} ms", flush=True)
 
@@ -126,12 +127,14 @@ def main():
     seeds = list(range(n))
     # uneven 64..1024 (same size class as the faces, tuned first so the
     # 640x490 entries below take precedence), 640x490 faces (LDP k = 1..4 and
-    # LBP), 8192^2 stress
+    # LBP), 260x260 face crops (codes only, the front end's extraction),
+    # 8192^2 stress
     sizes = [synth.sizes(s) for s in range(n)]
     _tune_workload("uneven", [h for h, _ in sizes], [w for _, w in sizes], seeds, 3, False, 3.0, a.out)
     for k in (3, 1, 2, 4):
         _tune_workload("medium", [490] * n, [640] * n, seeds, k, False, 3.0, a.out)
     _tune_workload("medium", [490] * n, [640] * n, seeds, 3, True, 3.0, a.out)
+    _tune_workload("crops", [260] * n, [260] * n, seeds, 3, False, 3.0, a.out, hist=False)
     for k in (1, 2, 3, 4):
         _tune_workload("large", [8192] * 4, [8192] * 4, list(range(4)), k, False, 6.0, a.out)
 

@@ -33,15 +33,15 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found")
 
 
-def variants() -> list[tuple[int, int, int, int, int]]:
-    """(id, rows per tile, warps per CTA, min CTAs per SM, staged) of every tile variant."""
+def variants() -> list[tuple[int, int, int, int, int, int]]:
+    """(id, rows per tile, warps per CTA, min CTAs per SM, staged, split) of every tile variant."""
     with open(os.path.join(CSRC, "ldp_launch.h")) as f:
         src = f.read()
     m = re.search(r"#define LDP_VARIANTS\(X\)((?:.*\\\n)*.*)", src)
     if not m:
         raise RuntimeError("LDP_VARIANTS not found")
     return [tuple(int(v) for v in t)
-            for t in re.findall(r"X\((\d+),\s*(\d+),\s*(\d+),\s*(\d+),\s*(\d+)\)", m.group(1))]
+            for t in re.findall(r"X\((\d+),\s*(\d+),\s*(\d+),\s*(\d+),\s*(\d+),\s*(\d+)\)", m.group(1))]
 
 
 def _sources_mtime() -> float:
@@ -88,17 +88,18 @@ def _build_locked(force: bool, verbose: bool, jobs: int | None, checked: bool) -
         (os.path.join(CSRC, "ldp_distance.cu"), os.path.join(bdir, "ldp_distance.o"), []),
         (os.path.join(CSRC, "ldp_pipeline.cu"), os.path.join(bdir, "ldp_pipeline.o"), []),
     ]
-    for vid, rpw, nw, mb, st in variants():
+    for vid, rpw, nw, mb, st, sp in variants():
         units.append((os.path.join(CSRC, "ldp_kernels.cu"), os.path.join(bdir, f"ldp_kernels_v{vid}.o"),
                       [f"-DLDP_VAR_ID={vid}", f"-DLDP_VAR_RPW={rpw}", f"-DLDP_VAR_NW={nw}", f"-DLDP_VAR_MB={mb}",
-                       f"-DLDP_VAR_ST={st}"]))
+                       f"-DLDP_VAR_ST={st}", f"-DLDP_VAR_SP={sp}"]))
     # the kernels of the other Eq. 2-3 readings (kernel modes 2..4, one unit
     # each), in the tile shape of variant 0
     v0 = variants()[0]
     for cm in (2, 3, 4):
         units.append((os.path.join(CSRC, "ldp_kernels.cu"), os.path.join(bdir, f"ldp_kernels_vcm{cm}.o"),
                       [f"-DLDP_VAR_ID=cm{cm}", f"-DLDP_VAR_RPW={v0[1]}", f"-DLDP_VAR_NW={v0[2]}",
-                       f"-DLDP_VAR_MB={v0[3]}", f"-DLDP_VAR_ST={v0[4]}", f"-DLDP_CODE_MODES={cm}"]))
+                       f"-DLDP_VAR_MB={v0[3]}", f"-DLDP_VAR_ST={v0[4]}", f"-DLDP_VAR_SP={v0[5]}",
+                       f"-DLDP_CODE_MODES={cm}"]))
     cmds = [[cc] + ARCH + FLAGS + extra + inc + defs + ["-c", src, "-o", obj] for src, obj, defs in units]
     jobs = jobs or max(1, min(len(cmds), os.cpu_count() or 1))
     with cf.ThreadPoolExecutor(jobs) as ex:

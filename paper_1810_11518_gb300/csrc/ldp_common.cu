@@ -29,9 +29,9 @@ int* status_word() {
     return addr[dev];
 }
 
-#define LDP_NAME(ID, RPW, NW, MB, ST) "r" #RPW "w" #NW "b" #MB "t" #ST,
-#define LDP_TH(ID, RPW, NW, MB, ST) (RPW),
-#define LDP_COUNT(ID, RPW, NW, MB, ST) +1
+#define LDP_NAME(ID, RPW, NW, MB, ST, SP) (SP ? "r" #RPW "w" #NW "b" #MB "t" #ST "s" : "r" #RPW "w" #NW "b" #MB "t" #ST),
+#define LDP_TH(ID, RPW, NW, MB, ST, SP) (RPW),
+#define LDP_COUNT(ID, RPW, NW, MB, ST, SP) +1
 static const char* kVariantNames[] = {LDP_VARIANTS(LDP_NAME)};
 static const int kVariantTH[] = {LDP_VARIANTS(LDP_TH)};
 constexpr int kNumVariants = 0 LDP_VARIANTS(LDP_COUNT);
@@ -137,7 +137,7 @@ cudaError_t launch_plain(int mode, int k, bool hist, int variant, const JobArgs&
     if (mode == kLDPThresh) return varcm3::launch_plain(mode, k, hist, jb, hc, s);
     if (mode == kLDPRawThresh) return varcm4::launch_plain(mode, k, hist, jb, hc, s);
     switch (variant) {
-#define LDP_CASE(ID, RPW, NW, MB, ST) \
+#define LDP_CASE(ID, RPW, NW, MB, ST, SP) \
     case ID: return var##ID::launch_plain(mode, k, hist, jb, hc, s);
         LDP_VARIANTS(LDP_CASE)
 #undef LDP_CASE
@@ -151,7 +151,7 @@ cudaError_t launch_batch_main(int mode, int k, bool hist, int variant, int grid,
     if (mode == kLDPThresh) return varcm3::launch_batch_main(mode, k, hist, grid, a, s);
     if (mode == kLDPRawThresh) return varcm4::launch_batch_main(mode, k, hist, grid, a, s);
     switch (variant) {
-#define LDP_CASE(ID, RPW, NW, MB, ST) \
+#define LDP_CASE(ID, RPW, NW, MB, ST, SP) \
     case ID: return var##ID::launch_batch_main(mode, k, hist, grid, a, s);
         LDP_VARIANTS(LDP_CASE)
 #undef LDP_CASE
@@ -164,7 +164,7 @@ cudaError_t batch_occupancy(int mode, int k, bool hist, int variant, int* blocks
     if (mode == kLDPThresh) return varcm3::batch_occupancy(mode, k, hist, blocks_per_sm);
     if (mode == kLDPRawThresh) return varcm4::batch_occupancy(mode, k, hist, blocks_per_sm);
     switch (variant) {
-#define LDP_CASE(ID, RPW, NW, MB, ST) \
+#define LDP_CASE(ID, RPW, NW, MB, ST, SP) \
     case ID: return var##ID::batch_occupancy(mode, k, hist, blocks_per_sm);
         LDP_VARIANTS(LDP_CASE)
 #undef LDP_CASE

@@ -425,13 +425,28 @@ __device__ __forceinline__ int band_lo(int b, int n, int nb) {
 // never read; LBP has a junk slot for them.
 // Region grids too fine for kWarpSlots slots count straight into global
 // memory.  `ph` holds the ring's per-stage wait parities across tiles.
-template <int MODE, int K, int RW, bool HIST, bool STAGED>
+template <int MODE, int K, int RW, bool HIST, bool STAGED, bool SPLIT>
 __device__ __forceinline__ void warp_tile(const Job& jb, const HistCfg& hc, int u0, int v0, uint32_t* wh,
                                           WarpRing* ring, uint32_t& ph, int* status) {
     const int lane = threadIdx.x & 31;
     const int H = jb.H, W = jb.W;
     const int ue = min(u0 + RW, H - 2);  // output rows [u0, ue) = image rows [u0+1, ue]
-    const int v = v0 + 4 * lane;
+    // SPLIT: a tile narrower than 64 columns (an image's last column tile)
+    // shares its rows between lane groups: lp lanes per row (a power of two
+    // covering its four-column groups), 32 / lp groups of consecutive rows.
+    // This lane's output rows are [ul, uh); otherwise all of the tile's.
+    int ul = u0, uh = ue, lc = lane;
+    if constexpr (SPLIT && !STAGED) {
+        const int ng = (min(kTileW, W - 2 - v0) + 3) / 4;
+        if (ng <= 16) {
+            const int lp = ng > 8 ? 16 : ng > 4 ? 8 : ng > 2 ? 4 : ng > 1 ? 2 : 1;
+            const int groups = 32 / lp, len = (ue - u0 + groups - 1) / groups;
+            ul = min(u0 + (lane / lp) * len, ue);
+            uh = min(ul + len, ue);
+            lc = lane % lp;
+        }
+    }
+    const int v = v0 + 4 * lc;
 
     // region slots of the tile (uniform across the warp)
     int ri_lo = 0, rj_lo = 0, ncs = 1, nslots = 1;
@@ -477,6 +492,7 @@ __device__ __forceinline__ void warp_tile(const Job& jb, const HistCfg& hc, int 
     }
     // region row of image row x = u + 1, advanced as the rows go down
     int ri = ri_lo, next_b = 0, rowb = 0;
+    if constexpr (HIST && SPLIT && !STAGED) ri = band_of(ul + 1, H, hc.R);
     // shared-memory byte address of bin 0 of each column's current slot
     uint32_t sbase[4] = {0u, 0u, 0u, 0u};
     const uint32_t wh_addr = HIST && use_smem && is_ldp(MODE) ? smem_addr(wh) : 0u;
@@ -494,7 +510,10 @@ __device__ __forceinline__ void warp_tile(const Job& jb, const HistCfg& hc, int 
     };
     if constexpr (HIST) {
         next_b = band_lo(ri + 1, H, hc.R);
-        rowb = use_smem ? 0 : ri * hc.C;
+        if constexpr (SPLIT && !STAGED)
+            rowb = use_smem ? (ri - ri_lo) * ncs * 256 : ri * hc.C;
+        else
+            rowb = use_smem ? 0 : ri * hc.C;
         if (use_smem) set_sbase();
     }
 
@@ -649,8 +668,8 @@ __device__ __forceinline__ void warp_tile(const Job& jb, const HistCfg& hc, int 
                     if (done) ph ^= 1u << sidx;
                 }
         }
-    } else if (v < W - 2) {  // per-lane global loads, one row ahead
-        const uint8_t* rp = jb.img + (size_t)u0 * P;
+    } else if (v < W - 2 && (!SPLIT || ul < uh)) {  // per-lane global loads, one row ahead
+        const uint8_t* rp = jb.img + (size_t)ul * P;
         const uint8_t* pf = rp + 3 * P;  // next input row to prefetch (one row ahead)
         Raw nx = load_raw(rp + 2 * P, v, W, fast_ld);
         Row r0, r1, r2;
@@ -660,23 +679,23 @@ __device__ __forceinline__ void warp_tile(const Job& jb, const HistCfg& hc, int 
         auto step = [&](const Row& A, const Row& B, Row& C, int u, auto always) {
             unpack(nx, C);
             if (decltype(always)::value ? index_ok(u + 3 < H, status)
-                                        : (u + 1 < ue && index_ok(u + 3 < H, status)))
+                                        : (u + 1 < uh && index_ok(u + 3 < H, status)))
                 nx = load_raw(pf, v, W, fast_ld);
             pf += P;
             emit(u, codes_of_row(A, B, C));
         };
         const std::true_type yes;
         const std::false_type no;
-        int u = u0;
-        for (; u + 4 <= ue; u += 3) {
+        int u = ul;
+        for (; u + 4 <= uh; u += 3) {
             step(r0, r1, r2, u, yes);
             step(r1, r2, r0, u + 1, yes);
             step(r2, r0, r1, u + 2, yes);
         }
         // one to three rows left
-        if (u < ue) step(r0, r1, r2, u, no);
-        if (u + 1 < ue) step(r1, r2, r0, u + 1, no);
-        if (u + 2 < ue) step(r2, r0, r1, u + 2, no);
+        if (u < uh) step(r0, r1, r2, u, no);
+        if (u + 1 < uh) step(r1, r2, r0, u + 1, no);
+        if (u + 2 < uh) step(r2, r0, r1, u + 2, no);
     }
 
     if constexpr (HIST) {

@@ -1,6 +1,7 @@
 // Kernels of libldp for ONE tile variant (rows per warp tile x warps per CTA), compiled
 // once per variant with -DLDP_VAR_ID=<n> -DLDP_VAR_RPW=<rows> -DLDP_VAR_NW=<warps>
-// -DLDP_VAR_MB=<min CTAs per SM> -DLDP_VAR_ST=<1: rows staged through the bulk-copy engine>:
+// -DLDP_VAR_MB=<min CTAs per SM> -DLDP_VAR_ST=<1: rows staged through the bulk-copy engine>
+// -DLDP_VAR_SP=<1: narrow tiles split their rows between lane groups>:
 // the single-image fused kernel and the persistent batch kernel for every
 // (mode, k, histogram) combination, plus their launchers.  Built once more
 // per other reading of Eq. 2-3 with -DLDP_CODE_MODES=<kernel mode> (raw-m
@@ -12,7 +13,7 @@
 #include "ldp_launch.h"
 
 #ifndef LDP_VAR_ID
-#error "compile with -DLDP_VAR_ID, -DLDP_VAR_RPW, -DLDP_VAR_NW, -DLDP_VAR_MB and -DLDP_VAR_ST"
+#error "compile with -DLDP_VAR_ID, -DLDP_VAR_RPW, -DLDP_VAR_NW, -DLDP_VAR_MB, -DLDP_VAR_ST and -DLDP_VAR_SP"
 #endif
 #define LDP_CAT2(a, b) a##b
 #define LDP_CAT(a, b) LDP_CAT2(a, b)
@@ -26,6 +27,7 @@ struct VAR {
     // ST: input rows staged through the bulk-copy ring
     static constexpr int RPW = LDP_VAR_RPW, NW = LDP_VAR_NW, MB = LDP_VAR_MB;
     static constexpr bool ST = LDP_VAR_ST != 0;
+    static constexpr bool SP = LDP_VAR_SP != 0;  // narrow tiles split their rows between lane groups
 };
 
 
@@ -91,8 +93,8 @@ __global__ void __launch_bounds__(V::NW * 32, V::MB) k_plain(JobArgs ja, HistArg
     WarpRing* ring;
     uint32_t* wh = warp_setup(sh, &ring);
     uint32_t ph = 0;
-    warp_tile<MODE, K, V::RPW, HIST, V::ST>(jb, to_hc(ha), (w / ntx) * V::RPW, (w % ntx) * kTileW, wh, ring, ph,
-                                            ja.status);
+    warp_tile<MODE, K, V::RPW, HIST, V::ST, V::SP>(jb, to_hc(ha), (w / ntx) * V::RPW, (w % ntx) * kTileW, wh, ring,
+                                                   ph, ja.status);
 }
 
 // ---------------- persistent batch kernel: warps take tiles independently ----------------
@@ -134,8 +136,8 @@ __global__ void __launch_bounds__(V::NW * 32, V::MB) k_batch(BatchArgs a) {
         jb.hist = a.hist ? a.hist + hoff : nullptr;
         const int lt = t - (int)wd(10);
         const int ntx = (jb.W - 2 + kTileW - 1) / kTileW;
-        warp_tile<MODE, K, V::RPW, HIST, V::ST>(jb, hc, (lt / ntx) * V::RPW, (lt % ntx) * kTileW, wh, ring, ph,
-                                                a.status);
+        warp_tile<MODE, K, V::RPW, HIST, V::ST, V::SP>(jb, hc, (lt / ntx) * V::RPW, (lt % ntx) * kTileW, wh, ring,
+                                                       ph, a.status);
     }
 }
 

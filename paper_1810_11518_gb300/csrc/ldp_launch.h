@@ -54,15 +54,17 @@ struct BatchArgs {
     int* status;  // device status word
 };
 
-// Tile variants X(id, rows per tile, warps per CTA, min CTAs per SM, staged):
-// each warp owns a tile of 128 columns x rows; MB caps registers; staged = 1
-// feeds the rows through the bulk-copy (TMA) engine into a shared ring.
+// Tile variants X(id, rows per tile, warps per CTA, min CTAs per SM, staged,
+// split): each warp owns a tile of 128 columns x rows; MB caps registers;
+// staged = 1 feeds the rows through the bulk-copy (TMA) engine into a shared
+// ring; split = 1 lets a tile narrower than 64 columns (an image's last) share
+// its rows between lane groups (for batches of narrow images).
 // ldp_kernels.cu is compiled once per entry (the build script reads this list).
-#define LDP_VARIANTS(X)                                                                          \
-    X(0, 64, 4, 5, 0) X(1, 64, 4, 6, 0) X(2, 64, 8, 3, 0) X(3, 64, 4, 4, 1) X(4, 128, 4, 4, 1) \
-    X(5, 64, 4, 7, 0) X(6, 64, 8, 4, 0) X(7, 16, 4, 6, 0) X(8, 8, 4, 6, 0)
+#define LDP_VARIANTS(X)                                                                                      \
+    X(0, 64, 4, 5, 0, 0) X(1, 64, 4, 6, 0, 0) X(2, 64, 8, 3, 0, 0) X(3, 64, 4, 4, 1, 0) X(4, 128, 4, 4, 1, 0) \
+    X(5, 64, 4, 7, 0, 0) X(6, 64, 8, 4, 0, 0) X(7, 16, 4, 6, 0, 0) X(8, 8, 4, 6, 0, 0) X(9, 64, 4, 7, 0, 1)
 
-#define LDP_DECLARE_VARIANT(ID, RPW, NW, MB, ST)                                                              \
+#define LDP_DECLARE_VARIANT(ID, RPW, NW, MB, ST, SP)                                                          \
     namespace var##ID {                                                                                   \
     cudaError_t launch_plain(int mode, int k, bool hist, const JobArgs& jb, const HistArgs& hc,           \
                              cudaStream_t s);                                                             \
@@ -72,9 +74,9 @@ struct BatchArgs {
 LDP_VARIANTS(LDP_DECLARE_VARIANT)
 // the code-variant modes kLDPRaw, kLDPThresh, kLDPRawThresh (one unit each),
 // in the tile shape of variant 0
-LDP_DECLARE_VARIANT(cm2, 64, 4, 5, 0)
-LDP_DECLARE_VARIANT(cm3, 64, 4, 5, 0)
-LDP_DECLARE_VARIANT(cm4, 64, 4, 5, 0)
+LDP_DECLARE_VARIANT(cm2, 64, 4, 5, 0, 0)
+LDP_DECLARE_VARIANT(cm3, 64, 4, 5, 0, 0)
+LDP_DECLARE_VARIANT(cm4, 64, 4, 5, 0, 0)
 #undef LDP_DECLARE_VARIANT
 constexpr int kCodeModeVariant = 0;  // variant whose tile shape varcm2..4 use
 

@@ -43,7 +43,7 @@ def test_variants_listed(lib):
     assert nv == len(libbuild.variants()) and nv >= 1
     for v in range(nv):
         name = lib.ldp_variant_name(v).decode()
-        assert re.fullmatch(r"r\d+w\d+b\d+t[01]", name)
+        assert re.fullmatch(r"r\d+w\d+b\d+t[01]s?", name)
     assert lib.ldp_variant_name(nv) == b""
     assert lib.ldp_set_plain_variant(nv) == 1
     assert lib.ldp_set_plain_variant(-2) == 1
