@@ -199,8 +199,10 @@ LDP_API int ldp_window_count(int n, int w, int s);
 
 /* Device scratch bytes ldp_window_hist / lbp_window_hist need for an H x W
  * image (k = 0: LBP or raw bins): a code map of (H-2) x (W-2) bytes unless
- * codes_given, plus the cell histograms when the windows overlap or leave
- * gaps (cells of gcd(size, stride) pixels).  0 on invalid arguments. */
+ * codes_given, plus the cell histograms (cells of gcd(size, stride) pixels)
+ * when the windows overlap or leave gaps and cannot take the single fused
+ * pass -- which needs the column stride to divide the window width and the
+ * window's rows of cells to fit in shared memory.  0 on invalid arguments. */
 LDP_API uint64_t ldp_window_scratch_bytes(int H, int W, int k, ldp_window_spec ws, int codes_given);
 
 /* LDP codes of one image (Eq. 1-3), then the histogram of every sliding
@@ -221,7 +223,8 @@ LDP_API int lbp_window_hist(const uint8_t *d_img, int H, int W, int pitch, ldp_w
                             void *stream);
 
 /* Scratch bytes of ldp_batch_window_hist: count x (cell words of a
- * max_H x max_W image) x 4, or 0 when stride = size. */
+ * max_H x max_W image) x 4, or 0 when no cell scratch is needed (stride =
+ * size, or the fused pass of ldp_window_scratch_bytes applies). */
 LDP_API uint64_t ldp_batch_window_scratch_bytes(int count, int max_H, int max_W, int k, ldp_window_spec ws);
 
 /* Window histograms of `count` images (host value) from code maps already
