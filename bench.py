@@ -78,14 +78,16 @@ def dist_env():
 # profiles/k_batch_ldp_k3_512img_full.md), scaled to a launch by its pixels.
 # Valid only for the kernel sources it was taken on: any change to them
 # reports traffic as null until a new capture is recorded here.
-TRAFFIC_PER_PX = 299.414e6 / (512 * 640 * 490)
+TRAFFIC_PER_PX = 303.933e6 / (512 * 640 * 490)
 TRAFFIC_SOURCES = ("paper_1810_11518_gb300/csrc/ldp_device.cuh", "paper_1810_11518_gb300/csrc/ldp_kernels.cu")
 TRAFFIC_SHA256 = "0f4de6b006a1fd41dbca14e4671a5f81e7755c1ceee4520fc186060f20f5114d"
 
 
 # Warp-instruction issue slots x 32 per input pixel of the same kernel, from
-# the same capture (smsp__inst_executed = 280,581,607 for 512 x 640x490).
-ISSUE_SLOTS_PER_PX = 280581607 * 32 / (512 * 640 * 490)
+# the same capture (smsp__inst_executed = 273,942,205 for 512 x 640x490).
+ISSUE_SLOTS_PER_PX = 273942205 * 32 / (512 * 640 * 490)
+# the tile variant the capture ran (both figures belong to it alone)
+TRAFFIC_VARIANT = "r128w4b7t0"
 
 
 def sources_match():
@@ -96,19 +98,20 @@ def sources_match():
     return h.hexdigest() == TRAFFIC_SHA256
 
 
-def measured_traffic(pixels, k, H, W):
-    if (k, H, W) != (3, 490, 640):
+def measured_traffic(pixels, k, H, W, variant=TRAFFIC_VARIANT):
+    if (k, H, W) != (3, 490, 640) or variant != TRAFFIC_VARIANT:
         return None
     return int(round(TRAFFIC_PER_PX * pixels)) if sources_match() else None
 
 
-def issue_roofline(pixels, k, H, W, kernel_ms, sms, sm_mhz):
+def issue_roofline(pixels, k, H, W, kernel_ms, sms, sm_mhz, variant=TRAFFIC_VARIANT):
     """The roof that binds the persistent kernel: instruction issue.  Peak =
     SMs x 4 schedulers x 32 lanes x the SM clock sampled in the timed region
     (one warp instruction per scheduler and cycle); achieved = the captured
     issue slots per pixel x pixels / kernel time.  None when the kernel
-    sources differ from the captured ones or the workload is another."""
-    if (k, H, W) != (3, 490, 640) or not sources_match() or not sm_mhz:
+    sources or the tile variant differ from the captured ones or the
+    workload is another."""
+    if (k, H, W) != (3, 490, 640) or variant != TRAFFIC_VARIANT or not sources_match() or not sm_mhz:
         return None
     achieved = ISSUE_SLOTS_PER_PX * pixels / (kernel_ms * 1e-3) / 1e12
     peak = sms * 4 * 32 * sm_mhz * 1e6 / 1e12
@@ -719,14 +722,14 @@ def main():
                        "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "achieved": round(achieved_gbs, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved_gbs / peak, 4),
-                         "traffic": measured_traffic(n * H * W, k, H, W),
+                         "traffic": measured_traffic(n * H * W, k, H, W, ldp.variant_name(variant)),
                          "kernel": "k_batch (persistent LDP codes + region hist)",
                          "kernel_ms": round(k_ms, 4), "algorithmic_bytes_per_launch": alg_bytes,
                          "peak_source": f"{peak_src} hbm_gbs",
-                         "binding_roof": "integer pipes and issue (ALU 73%, issue 81% in ncu); see profiles/"},
+                         "binding_roof": "integer pipes and issue (ALU 71%, issue 78% in ncu); see issue_roofline"},
             "issue_roofline": issue_roofline(n * H * W, k, H, W, k_ms,
                                              torch.cuda.get_device_properties(dev).multi_processor_count,
-                                             (clk or {}).get("sm_mhz")),
+                                             (clk or {}).get("sm_mhz"), ldp.variant_name(variant)),
             "e2e": e2e,
             "gpu_launches": 3 * a.steps,
             "clocks": clk,

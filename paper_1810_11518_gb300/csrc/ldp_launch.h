@@ -62,7 +62,8 @@ struct BatchArgs {
 // ldp_kernels.cu is compiled once per entry (the build script reads this list).
 #define LDP_VARIANTS(X)                                                                                      \
     X(0, 64, 4, 5, 0, 0) X(1, 64, 4, 6, 0, 0) X(2, 64, 8, 3, 0, 0) X(3, 64, 4, 4, 1, 0) X(4, 128, 4, 4, 1, 0) \
-    X(5, 64, 4, 7, 0, 0) X(6, 64, 8, 4, 0, 0) X(7, 16, 4, 6, 0, 0) X(8, 8, 4, 6, 0, 0) X(9, 64, 4, 7, 0, 1)
+    X(5, 64, 4, 7, 0, 0) X(6, 64, 8, 4, 0, 0) X(7, 16, 4, 6, 0, 0) X(8, 8, 4, 6, 0, 0) X(9, 64, 4, 7, 0, 1)   \
+    X(10, 128, 4, 7, 0, 0)
 
 #define LDP_DECLARE_VARIANT(ID, RPW, NW, MB, ST, SP)                                                          \
     namespace var##ID {                                                                                   \

@@ -34,8 +34,10 @@ def test_measured_figures_follow_the_sources(bench, monkeypatch):
     assert r["peak"] == pytest.approx(152 * 4 * 32 * 2070e6 / 1e12, rel=1e-3)
     assert r["achieved"] == pytest.approx(bench.ISSUE_SLOTS_PER_PX * px / 2.0e-3 / 1e12, rel=1e-3)
     assert r["frac"] == pytest.approx(r["achieved"] / r["peak"], rel=1e-3)
-    # another workload, or no clock sample: no figure
+    # another workload or tile variant, or no clock sample: no figure
     assert bench.measured_traffic(px, 2, 490, 640) is None
+    assert bench.measured_traffic(px, 3, 490, 640, "r8w4b6t0") is None
+    assert bench.issue_roofline(px, 3, 490, 640, 2.0, 152, 2070.0, "r8w4b6t0") is None
     assert bench.issue_roofline(px, 3, 480, 640, 2.0, 152, 2070.0) is None
     assert bench.issue_roofline(px, 3, 490, 640, 2.0, 152, None) is None
     # kernel sources changed since the capture: both withheld
