@@ -221,3 +221,24 @@ def test_pipeline_arguments_without_gpu(lib):
     f = ctypes.c_void_p(0x1000)
     assert lib.ldp_pipeline_run(None, 1, f, f, f, f, f, None, None, None, f, None) == EINVAL
     assert lib.ldp_pipeline_destroy(None) == 0
+
+
+def test_autotune_cache_names_compiled_variants():
+    """Every tuned entry shipped with the package names a variant of the
+    compiled list, by index and by name, so a change of the variant list
+    cannot silently re-point the cache."""
+    import json
+    import os
+
+    from paper_1810_11518_gb300 import autotune
+    from paper_1810_11518_gb300 import build as libbuild
+
+    names = [f"r{rpw}w{nw}b{mb}t{st}" + ("s" if sp else "") for _, rpw, nw, mb, st, sp in libbuild.variants()]
+    with open(autotune.DEFAULT_CACHE) as f:
+        cache = json.load(f)
+    assert cache
+    for key, ent in cache.items():
+        assert 0 <= ent["variant"] < len(names), key
+        assert ent["name"] == names[ent["variant"]], key
+        assert ent["ctas_per_sm"] >= 0
+    assert os.path.basename(autotune.DEFAULT_CACHE) == "autotune_cache.json"
