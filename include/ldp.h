@@ -252,7 +252,12 @@ typedef struct ldp_batch_plan ldp_batch_plan;
 
 /* Creates a plan for batches of up to max_images images holding up to
  * max_pixels pixels in total.  The plan owns its device work-list scratch
- * (allocated here) and a CUDA graph of its launches (built on first run).
+ * (allocated here, sized for the tile height of variant 0: at most
+ * max_pixels (TH + 129) / (384 TH) + max_images + 1 tiles of TH rows x 128
+ * columns, enough for any batch within the two bounds) and a CUDA graph of
+ * its launches (built on first run).  A batch whose descriptors hold more
+ * than max_pixels pixels is clamped on the device and sets bit 1 of the
+ * device status word; the checked build reports it as LDP_EINVAL.
  * EINVAL: out NULL, max_images < 1, bad k / rs; ENOMEM on allocation
  * failure. */
 LDP_API int ldp_batch_plan_create(ldp_batch_plan **out, int max_images, uint64_t max_pixels, int k,
@@ -287,7 +292,10 @@ LDP_API int ldp_batch_plan_destroy(ldp_batch_plan *plan);
 
 /* Kernel configuration (tile shape / CTAs per SM) a plan uses; set by the
  * autotuner.  variant in [0, ldp_num_variants()), ctas_per_sm 0 = as many
- * as fit. */
+ * as fit.  A variant of shorter tiles than the plan's work list was sized
+ * for reallocates the work list (synchronising the device); on failure
+ * (ENOMEM, or EINVAL when the list would exceed 1.5e9 tiles) the plan keeps
+ * its previous configuration. */
 LDP_API int ldp_batch_plan_set_config(ldp_batch_plan *plan, int variant, int ctas_per_sm);
 LDP_API int ldp_num_variants(void);
 /* Short description of a variant, static storage: "r<rows per warp tile>
@@ -439,8 +447,39 @@ LDP_API const char *ldp_last_error(void);
 /* Reads and clears the device status word (bit 0: a batch descriptor was
  * rejected on the device; bit 1: a batch needed more tiles than its plan
  * holds; bit 2: a bounded wait for staged input gave up; bit 3: a crop
- * descriptor was rejected).  Synchronises `stream`. */
+ * descriptor was rejected; bit 4, checked build: an index outside its
+ * buffer was skipped).  Synchronises `stream`.  The checked build also
+ * waits at the end of every batch and single-image run and returns
+ * LDP_EINVAL for bit 1 and LDP_ETIMEOUT for bit 2 (without clearing them). */
 LDP_API int ldp_device_status(void *stream, int *out);
+
+/* ---- fault injection (tests of the error paths; the paper has no
+ * counterpart) ----
+ * Makes later calls fail on the host, the way a real failure would, so that
+ * tests can check the error codes and the clean shutdown without faulting a
+ * GPU.  After `after` more operations of the kind succeed, the next `count`
+ * fail:
+ *   LDP_FAULT_DEVICE_ALLOC: device allocations of batch plans and of the
+ *     serving runtime fail as if the device were out of memory
+ *     (ldp_batch_plan_create, ldp_batch_plan_set_config and
+ *     ldp_server_create then return LDP_ENOMEM and free what they had);
+ *   LDP_FAULT_SERVER_LAUNCH: serving batches fail to launch as if the launch
+ *     had returned a CUDA error, without queueing any work: the runtime
+ *     records the error, gives the batch's arena space back, later
+ *     ldp_server_submit / ldp_server_poll calls return LDP_ECUDA and
+ *     ldp_server_destroy still shuts down;
+ *   LDP_FAULT_STAGE_WAIT (checked build only, LDP_ENOTIMPL otherwise; after
+ *     must be 0): the staged tile variants stop filling input-stage group
+ *     `count` of every tile (0 turns it off) and give up waiting for it
+ *     after a few polls, with no copy in flight for that stage; the run sets
+ *     bit 2 of the device status word and returns LDP_ETIMEOUT.
+ *     Synchronises `stream`.
+ * count = 0 clears pending faults of the kind.  EINVAL for an unknown kind
+ * or a negative after / count. */
+#define LDP_FAULT_DEVICE_ALLOC 0
+#define LDP_FAULT_SERVER_LAUNCH 1
+#define LDP_FAULT_STAGE_WAIT 2
+LDP_API int ldp_test_inject_fault(int kind, int after, int count, void *stream);
 
 /* Library version (major*10000 + minor*100 + patch). */
 LDP_API int ldp_version(void);

@@ -386,6 +386,20 @@ def device_status(stream=None) -> int:
     return out.value
 
 
+FAULT_DEVICE_ALLOC = _abi.LDP_FAULT_DEVICE_ALLOC
+FAULT_SERVER_LAUNCH = _abi.LDP_FAULT_SERVER_LAUNCH
+FAULT_STAGE_WAIT = _abi.LDP_FAULT_STAGE_WAIT
+
+
+def inject_fault(kind: int, count: int, after: int = 0, stream=None) -> None:
+    """Test hook: after `after` more library operations of `kind` succeed,
+    makes the next `count` fail on the host the way a real failure would
+    (device allocations, serving batch launches) or, in the checked build,
+    makes the staged tile variants give up on input-stage group `count`
+    (ldp_test_inject_fault in ldp.h)."""
+    _abi.call("ldp_test_inject_fault", int(kind), int(after), int(count), _stream(stream))
+
+
 def batch_run_noalloc(d_descs, count: int, max_pixels: int, max_side: int, d_hist, k: int = 3,
                       regions=(7, 6), compact: bool = True, stream=None) -> None:
     """Batched LDP run that allocates no device memory (static work list of

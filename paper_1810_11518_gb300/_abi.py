@@ -42,8 +42,9 @@ EXPORTS = [
     "ldp_window_count", "ldp_window_scratch_bytes", "ldp_window_hist", "lbp_window_hist",
     "ldp_batch_window_scratch_bytes", "ldp_batch_window_hist", "ldp_codes_ex", "ldp_region_hist_ex",
     "ldp_resize", "ldp_batch_resize", "ldp_hist_distance", "ldp_pipeline_create", "ldp_pipeline_run",
-    "ldp_pipeline_destroy", "ldp_pipeline_set_config",
+    "ldp_pipeline_destroy", "ldp_pipeline_set_config", "ldp_test_inject_fault",
 ]
+LDP_FAULT_DEVICE_ALLOC, LDP_FAULT_SERVER_LAUNCH, LDP_FAULT_STAGE_WAIT = 0, 1, 2
 
 
 class LdpError(RuntimeError):
@@ -142,6 +143,7 @@ def load(path: str | None = None):
             "lbp_window_hist": [vp, i32, i32, i32, WindowSpec, vp, vp, i32, vp, u64, vp],
             "ldp_batch_window_scratch_bytes": [i32, i32, i32, i32, WindowSpec],
             "ldp_batch_window_hist": [vp, i32, i32, i32, i32, WindowSpec, vp, vp, u64, vp],
+            "ldp_test_inject_fault": [i32, i32, i32, vp],
         }
         for name, args in sig.items():
             fn = getattr(lib, name)

@@ -55,21 +55,38 @@ def lookup(device: str, sms: int, path: str, k: int, mode: str, pixels_per_image
 
 def tune_plan(plan, d_desc, d_count, d_hist, ctas_options=(0, 4), reps: int = 8, warmup: int = 2) -> dict:
     """Times every (variant, ctas_per_sm) on this batch; leaves the best set
-    on the plan and returns it with all measurements (kernel ms, median)."""
+    on the plan and returns it with all measurements (kernel ms, median).
+
+    A candidate whose runs set a bit of the device status word (work cut
+    short: more tiles than the work list holds, an image rejected, a wait
+    that gave up) did not do the whole batch: it is recorded with its status
+    and never chosen.  RuntimeError when every candidate does so."""
     import paper_1810_11518_gb300 as ldp
 
     results = []
+    ldp.device_status()  # start from a clear status word
     for v in range(ldp.num_variants()):
         for cps in ctas_options:
             plan.set_config(v, cps)
             for _ in range(warmup):
                 plan.run(d_desc, d_count, d_hist)
+            status = ldp.device_status()
+            if status:
+                results.append({"variant": v, "name": ldp.variant_name(v), "ctas_per_sm": cps,
+                                "kernel_ms": None, "status": status})
+                continue
             plan.enable_timing(reps)
             for _ in range(reps):
                 plan.run(d_desc, d_count, d_hist)
             ms = statistics.median(plan.kernel_times(reps))
-            results.append({"variant": v, "name": ldp.variant_name(v), "ctas_per_sm": cps, "kernel_ms": ms})
-    best = min(results, key=lambda r: r["kernel_ms"])
+            status = ldp.device_status()
+            results.append({"variant": v, "name": ldp.variant_name(v), "ctas_per_sm": cps,
+                            "kernel_ms": None if status else ms, "status": status})
+    timed = [r for r in results if r["status"] == 0]
+    if not timed:
+        raise RuntimeError("autotune: every variant set the device status word "
+                           f"({sorted({r['status'] for r in results})}); the batch exceeds the plan or is invalid")
+    best = min(timed, key=lambda r: r["kernel_ms"])
     plan.set_config(best["variant"], best["ctas_per_sm"])
     return {"variant": best["variant"], "name": best["name"], "ctas_per_sm": best["ctas_per_sm"],
             "kernel_ms": best["kernel_ms"], "all": results}

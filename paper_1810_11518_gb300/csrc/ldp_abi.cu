@@ -116,6 +116,13 @@ int run_plain(int mode, const uint8_t* img, int H, int W, int pitch, int k, int 
     }
     cudaError_t e = launch_plain(mode, k, hist != nullptr, plain_variant(H, W), jb, hc, s);
     if (e != cudaSuccess) return report_cuda(e, "kernel launch");
+#ifdef LDP_CHECKED
+    // checked builds wait for the launch and report a bounded wait that gave up
+    int st = 0;
+    e = peek_status(s, &st);
+    if (e != cudaSuccess) return report_cuda(e, "reading the device status");
+    if (st & kStatusWaitTimeout) return report_error(LDP_ETIMEOUT, "a bounded wait for staged input gave up");
+#endif
     return LDP_OK;
 }
 
@@ -136,6 +143,7 @@ struct ldp_batch_plan {
     ldp_region_spec rs{1, 1, 0};
     unsigned flags = 0;
     int max_images = 0, max_tiles = 0;
+    int cap_th = 0;  // tile height the work list is sized for
     uint64_t max_pixels = 0;
     int variant = 0, ctas_per_sm = 0;
     int device = 0, num_sms = 0;
@@ -153,6 +161,54 @@ struct ldp_batch_plan {
     std::vector<cudaEvent_t> ev_start, ev_end;
     int nrec = 0;
 };
+
+namespace {
+
+// Upper bound on the warp tiles (TH rows x 128 columns) of any batch of at
+// most n images holding at most P pixels.  An H x W image (H, W >= 3) has
+// ceil(h/TH) * ceil(w/128) tiles, h = H-2, w = W-2, at most
+// (h + TH-1)(w + 127) / (128 TH) = (hw + 127 h + (TH-1) w + 127 (TH-1)) / (128 TH);
+// with hw <= HW and h, w <= HW/3 (the other side is at least 3) that is
+// below HW (TH + 129) / (384 TH) + 1.  Summed over the images:
+double tile_capacity(uint64_t P, int n, int TH) {
+    return (double)P * (double)(TH + 129) / (384.0 * (double)TH) + (double)n + 1.0;
+}
+
+// (Re)allocates the plan's work list (counter, total, prefix, tile map) for
+// tiles of TH rows.  On failure the plan keeps its previous work list.  The
+// old list may be in use by queued work and by the captured graph: the
+// device is synchronised and the graph dropped before it is freed.
+int plan_size_work_list(ldp_batch_plan* p, int TH) {
+    const double bound = tile_capacity(p->max_pixels, p->max_images, TH);
+    if (bound > 1.5e9) return fail(LDP_EINVAL, "max_pixels too large for a plan of this tile height");
+    const int max_tiles = (int)bound;
+    const size_t n_ints = (size_t)(p->max_images + 1) + (size_t)max_tiles + 2;
+    void* mem = nullptr;
+    cudaError_t e = ldp::device_malloc(&mem, n_ints * sizeof(int));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(LDP_ENOMEM, "device allocation of the plan's work list failed");
+    }
+    if (p->scratch) {
+        cudaDeviceSynchronize();
+        if (p->exec) cudaGraphExecDestroy(p->exec);
+        if (p->graph) cudaGraphDestroy(p->graph);
+        p->exec = nullptr;
+        p->graph = nullptr;
+        cudaFree(p->scratch);
+    }
+    p->scratch = mem;
+    p->max_tiles = max_tiles;
+    p->cap_th = TH;
+    int* base = static_cast<int*>(mem);
+    p->scr.counter = base;
+    p->scr.total = base + 1;
+    p->scr.prefix = base + 2;
+    p->scr.tile_img = base + 2 + (p->max_images + 1);
+    return LDP_OK;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -282,11 +338,8 @@ int ldp_batch_plan_create(ldp_batch_plan** out, int max_images, uint64_t max_pix
     if (rs.compact != 0 && rs.compact != 1) return fail(LDP_EINVAL, "compact must be 0 or 1");
     if (rs.compact && (mode == ldp::kLDPThresh || mode == ldp::kLDPRawThresh))
         return fail(LDP_EINVAL, "threshold code modes count 256 raw bins (compact = 0)");
-    // Tiles of an image: ceil((H-2)/TH)*ceil((W-2)/128) <= HW/(TH*128) + (H+W)/min(TH,128) + 1,
-    // and H + W <= 2HW/3 for H, W >= 3; every variant has TH >= 64.
-    const double bound = (double)max_pixels / (64.0 * 128.0) + (2.0 / 3.0) * (double)max_pixels / 64.0 +
-                         (double)max_images + 1.0;
-    if (bound > 1.5e9) return fail(LDP_EINVAL, "max_pixels too large for one plan");
+    const int th0 = ldp::variant_tile_h(0);
+    if (tile_capacity(max_pixels, max_images, th0) > 1.5e9) return fail(LDP_EINVAL, "max_pixels too large for one plan");
     ldp_batch_plan* p = new (std::nothrow) ldp_batch_plan();
     if (!p) return fail(LDP_ENOMEM, "host allocation failed");
     p->mode = mode;
@@ -296,25 +349,16 @@ int ldp_batch_plan_create(ldp_batch_plan** out, int max_images, uint64_t max_pix
     p->flags = flags;
     p->max_images = max_images;
     p->max_pixels = max_pixels;
-    p->max_tiles = (int)bound;
     cudaError_t e = cudaGetDevice(&p->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device);
     if (e != cudaSuccess) {
         delete p;
         return cuda_fail(e, "querying the device");
     }
-    const size_t n_ints = (size_t)(max_images + 1) + (size_t)p->max_tiles + 2;
-    e = cudaMalloc(&p->scratch, n_ints * sizeof(int));
-    if (e != cudaSuccess) {
+    if ((rc = plan_size_work_list(p, th0)) != LDP_OK) {
         delete p;
-        cudaGetLastError();
-        return fail(LDP_ENOMEM, "device allocation of the plan's work list failed");
+        return rc;
     }
-    int* base = static_cast<int*>(p->scratch);
-    p->scr.counter = base;
-    p->scr.total = base + 1;
-    p->scr.prefix = base + 2;
-    p->scr.tile_img = base + 2 + (max_images + 1);
     *out = p;
     return LDP_OK;
 }
@@ -323,13 +367,20 @@ int ldp_batch_plan_set_config(ldp_batch_plan* plan, int variant, int ctas_per_sm
     if (!plan) return fail(LDP_EINVAL, "plan is NULL");
     if (variant < 0 || variant >= ldp::num_variants()) return fail(LDP_EINVAL, "variant out of range");
     if (ctas_per_sm < 0 || ctas_per_sm > 64) return fail(LDP_EINVAL, "ctas_per_sm out of range");
+    // a variant of shorter tiles than the work list was sized for needs a
+    // larger one (code-mode plans always run the tile shape of kCodeModeVariant)
+    const int th = ldp::variant_tile_h(plan->mode >= 2 ? ldp::kCodeModeVariant : variant);
+    if (th < plan->cap_th) {
+        const int rc = plan_size_work_list(plan, th);
+        if (rc != LDP_OK) return rc;  // the plan keeps its previous configuration
+    }
     plan->variant = variant;
     plan->ctas_per_sm = ctas_per_sm;
     return LDP_OK;
 }
 
-static int batch_run(ldp_batch_plan* plan, int mode, const ldp_image_desc* d_descs, const int* d_count,
-                     uint32_t* d_hist, void* stream) {
+static int batch_launch(ldp_batch_plan* plan, int mode, const ldp_image_desc* d_descs, const int* d_count,
+                        uint32_t* d_hist, void* stream) {
     ldp::Range range("ldp.batch_run");
     if (!plan) return fail(LDP_EINVAL, "plan is NULL");
     if ((plan->mode == 1) != (mode == 1))
@@ -447,6 +498,31 @@ static int batch_run(ldp_batch_plan* plan, int mode, const ldp_image_desc* d_des
     return LDP_OK;
 }
 
+// Checked builds wait for the work just queued on `stream` and turn the
+// status bits a caller can cause into errors: a batch with more tiles than
+// its work list holds (its descriptors exceed the plan's max_pixels) and a
+// bounded wait that gave up.  Release builds stay asynchronous; the bits
+// are read with ldp_device_status.
+static int checked_status(void* stream) {
+#ifdef LDP_CHECKED
+    int st = 0;
+    const cudaError_t e = ldp::peek_status(static_cast<cudaStream_t>(stream), &st);
+    if (e != cudaSuccess) return cuda_fail(e, "reading the device status");
+    if (st & ldp::kStatusTooManyTiles)
+        return fail(LDP_EINVAL, "the batch needed more tiles than the plan holds (pixels beyond max_pixels)");
+    if (st & ldp::kStatusWaitTimeout) return fail(LDP_ETIMEOUT, "a bounded wait for staged input gave up");
+#else
+    (void)stream;
+#endif
+    return LDP_OK;
+}
+
+static int batch_run(ldp_batch_plan* plan, int mode, const ldp_image_desc* d_descs, const int* d_count,
+                     uint32_t* d_hist, void* stream) {
+    const int rc = batch_launch(plan, mode, d_descs, d_count, d_hist, stream);
+    return rc != LDP_OK ? rc : checked_status(stream);
+}
+
 int ldp_batch_plan_enable_timing(ldp_batch_plan* plan, int capacity) {
     if (!plan) return fail(LDP_EINVAL, "plan is NULL");
     if (capacity < 0 || capacity > (1 << 20)) return fail(LDP_EINVAL, "capacity out of range");
@@ -501,6 +577,26 @@ int ldp_batch_plan_destroy(ldp_batch_plan* plan) {
     if (plan->scratch) cudaFree(plan->scratch);
     delete plan;
     return LDP_OK;
+}
+
+int ldp_test_inject_fault(int kind, int after, int count, void* stream) {
+    if (count < 0 || after < 0) return fail(LDP_EINVAL, "after and count must be >= 0");
+    switch (kind) {
+        case LDP_FAULT_DEVICE_ALLOC:
+        case LDP_FAULT_SERVER_LAUNCH: ldp::set_faults(kind, after, count); return LDP_OK;
+        case LDP_FAULT_STAGE_WAIT: {
+            if (after != 0) return fail(LDP_EINVAL, "the stage-wait fault takes after = 0");
+#ifdef LDP_CHECKED
+            const cudaError_t e = ldp::set_wait_fault(count, static_cast<cudaStream_t>(stream));
+            if (e != cudaSuccess) return cuda_fail(e, "setting the stage-wait fault");
+            return LDP_OK;
+#else
+            (void)stream;
+            return fail(LDP_ENOTIMPL, "the stage-wait fault exists in the checked build only");
+#endif
+        }
+        default: return fail(LDP_EINVAL, "unknown fault kind");
+    }
 }
 
 int ldp_device_status(void* stream, int* out) {

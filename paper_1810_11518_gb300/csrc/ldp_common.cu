@@ -6,14 +6,15 @@
 #include "ldp_device.cuh"
 #include "ldp_launch.h"
 
+#include <atomic>
 #include <mutex>
 
 namespace ldp {
 
-// Device status word: bit 0 = a batch descriptor was rejected on the device,
-// bit 1 = a batch needed more tiles than its plan holds, bit 2 = a bounded
-// wait for staged input gave up, bit 3 = a crop descriptor was rejected.
-__device__ int g_status;
+// Device status word (word 0): the kStatus* bits of ldp_modes.h.  Word 1
+// is read by the staged tile loop of checked builds: an input-stage group
+// to withhold (0: none), set by the wait-fault test hook.
+__device__ int g_status[2];
 
 int* status_word() {
     static std::mutex mu;
@@ -23,7 +24,7 @@ int* status_word() {
     std::lock_guard<std::mutex> lk(mu);
     if (!addr[dev]) {
         void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_status) != cudaSuccess) return nullptr;
+        if (cudaGetSymbolAddress(&p, g_status) != cudaSuccess) return nullptr;  // word 0
         addr[dev] = static_cast<int*>(p);
     }
     return addr[dev];
@@ -94,11 +95,11 @@ __global__ void __launch_bounds__(1024) k_batch_scan(BatchArgs a, int TH) {
         if (tid == 1023) s_carry = carry + warp_excl + incl;
         __syncthreads();
     }
-    if (bad) atomicOr(&g_status, 1);
+    if (bad) atomicOr(&g_status[0], kStatusBadDesc);
     if (tid == 0) {
         int total = s_carry;
         if (total > a.max_tiles) {
-            atomicOr(&g_status, 2);
+            atomicOr(&g_status[0], kStatusTooManyTiles);
             total = a.max_tiles;
         }
         a.scr.prefix[n] = s_carry;
@@ -171,6 +172,56 @@ cudaError_t batch_occupancy(int mode, int k, bool hist, int variant, int* blocks
         default: return cudaErrorInvalidValue;
     }
 }
+
+cudaError_t peek_status(cudaStream_t s, int* out) {
+    cudaError_t e = cudaMemcpyFromSymbolAsync(out, g_status, sizeof(int), 0, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return e;
+    return cudaStreamSynchronize(s);
+}
+
+// ---------------- fault injection for tests (ldp_test_inject_fault) ----------------
+// Per kind: operations still allowed to succeed, then operations to fail.
+static std::mutex g_fault_mu;
+static int g_fault_after[kFaultKinds], g_fault_count[kFaultKinds];
+
+bool take_fault(int kind) {
+    if (kind < 0 || kind >= kFaultKinds) return false;
+    std::lock_guard<std::mutex> lk(g_fault_mu);
+    if (g_fault_count[kind] <= 0) return false;
+    if (g_fault_after[kind] > 0) {
+        --g_fault_after[kind];
+        return false;
+    }
+    --g_fault_count[kind];
+    return true;
+}
+
+void set_faults(int kind, int after, int count) {
+    if (kind < 0 || kind >= kFaultKinds) return;
+    std::lock_guard<std::mutex> lk(g_fault_mu);
+    g_fault_after[kind] = after > 0 ? after : 0;
+    g_fault_count[kind] = count > 0 ? count : 0;
+}
+
+cudaError_t device_malloc(void** p, size_t bytes) {
+    if (take_fault(kFaultDeviceAlloc)) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
+
+#ifdef LDP_CHECKED
+// Checked builds: the staged tile loop skips the fill of input-stage group
+// `group` (when >= 1) and waits for it only kTestSpinLimit polls, so that
+// bounded wait gives up with no copy in flight for the stage.
+cudaError_t set_wait_fault(int group, cudaStream_t s) {
+    cudaError_t e =
+        cudaMemcpyToSymbolAsync(g_status, &group, sizeof(int), sizeof(int), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    return cudaStreamSynchronize(s);
+}
+#endif
 
 cudaError_t read_clear_status(cudaStream_t s, int* out) {
     static const int zero = 0;

@@ -344,8 +344,7 @@ __host__ __device__ constexpr int warp_hist_slots() { return is_ldp(MODE) ? kWar
 // mbarrier per stage.
 constexpr int kStageRows = 8, kStages = 3, kRowBytes = 144;
 constexpr int kSpinLimit = 1 << 22;  // bounded mbarrier waits
-constexpr int kStatusWaitTimeout = 4;  // device status bit: a bounded wait gave up
-constexpr int kStatusBounds = 16;      // checked builds: an index outside its buffer was skipped
+constexpr int kTestSpinLimit = 256;  // checked builds: the wait of a withheld stage (test hook)
 
 // Checked builds (-DLDP_CHECKED) test every shared- and global-memory index
 // of the tile loop (and of the window and resize kernels) against its buffer;
@@ -588,9 +587,16 @@ __device__ __forceinline__ void warp_tile(const Job& jb, const HistCfg& hc, int 
         const uint8_t* base = jb.img + (size_t)u0 * P + v0;
         uint32_t pend = 0;  // stages filled and not yet waited
         bool ok = true;
+#ifdef LDP_CHECKED
+        // test hook (word 1 of the status word): stage group `withheld` is
+        // never filled, so its bounded wait runs out with no copy in flight
+        const int withheld = status[1];
+#else
+        constexpr int withheld = 0;
+#endif
         auto fill = [&](int g) {
             const int r0 = g * kStageRows, n = min(kStageRows, nrows - r0);
-            if (n <= 0) return;
+            if (n <= 0 || (withheld > 0 && g == withheld)) return;
             const int sidx = g % kStages;
             // rows [r0, r0 + nb) go through the bulk-copy engine
             int nb = bulk_img ? n : 0;
@@ -616,8 +622,9 @@ __device__ __forceinline__ void warp_tile(const Job& jb, const HistCfg& hc, int 
         auto wait = [&](int g) {
             const int sidx = g % kStages;
             const uint32_t par = (ph >> sidx) & 1u;
+            const int limit = (withheld > 0 && g == withheld) ? kTestSpinLimit : kSpinLimit;
             bool done = false;
-            for (int i = 0; i < kSpinLimit && !done; ++i) done = mbar_try_wait(&ring->bar[sidx], par);
+            for (int i = 0; i < limit && !done; ++i) done = mbar_try_wait(&ring->bar[sidx], par);
             if (done) {
                 ph ^= 1u << sidx;
                 pend &= ~(1u << sidx);

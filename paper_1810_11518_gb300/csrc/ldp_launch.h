@@ -125,6 +125,23 @@ cudaError_t launch_distance(const uint32_t* q, int nq, int ldq, const uint32_t* 
                             int metric, void* out, int ldo, cudaStream_t s);
 
 cudaError_t read_clear_status(cudaStream_t s, int* out);
+// Reads the device status word without clearing it (synchronises s).
+cudaError_t peek_status(cudaStream_t s, int* out);
+
+// Fault injection for tests (ldp_test_inject_fault): after `after` more
+// operations of a kind, take_fault(kind) is true (and uses one up) for the
+// next `count` ones.
+constexpr int kFaultDeviceAlloc = LDP_FAULT_DEVICE_ALLOC;  // device allocations of plans and the server
+constexpr int kFaultServerLaunch = LDP_FAULT_SERVER_LAUNCH;  // a serving batch fails to launch
+constexpr int kFaultKinds = 3;
+bool take_fault(int kind);
+void set_faults(int kind, int after, int count);
+// cudaMalloc, or cudaErrorMemoryAllocation while a device-allocation fault is pending
+cudaError_t device_malloc(void** p, size_t bytes);
+#ifdef LDP_CHECKED
+// Makes the staged tile loop withhold input-stage group `group` (0: off).
+cudaError_t set_wait_fault(int group, cudaStream_t s);
+#endif
 // Device address of the status word on the current device (looked up once per device).
 int* status_word();
 

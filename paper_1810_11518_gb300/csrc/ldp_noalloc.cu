@@ -23,14 +23,14 @@
 #include <cstdio>
 #include <mutex>
 
+#include "ldp_device.cuh"
 #include "ldp_launch.h"
 
 namespace {
 
 constexpr int kNoAllocInts = 1 << 21;  // 8 MiB of work list
 constexpr int kMaxDevices = 64;
-constexpr int kTileRows = 64;   // variant 0: warp tiles of 64 rows
-constexpr int kTileCols = 128;  // output columns per tile
+constexpr int kTileCols = ldp::kTileW;  // output columns per warp tile
 
 // [0] tile counter, [1] total tiles, [2] image count, [3..count+3] prefix,
 // then the tile -> image map.
@@ -60,8 +60,11 @@ extern "C" LDP_API int ldp_batch_run_noalloc(const ldp_image_desc* d_descs, int 
         return ldp::report_error(LDP_EINVAL, "region grid must be 1x1 .. 1<<22 regions");
     if (rs.compact != 0 && rs.compact != 1) return ldp::report_error(LDP_EINVAL, "compact must be 0 or 1");
     if (max_side < 3 || max_side > (1 << 20)) return ldp::report_error(LDP_EINVAL, "max_side must be in [3, 1<<20]");
-    // ceil(a)*ceil(b) <= ab + a + b + 1 with a = (H-2)/64, b = (W-2)/128, so an
-    // image has at most H*W/8192 + floor(max_side/64) + floor(max_side/128) + 3 tiles
+    // the run uses tile variant 0 (tiles of TH rows x 128 columns);
+    // ceil(a)*ceil(b) <= ab + a + b + 1 with a = (H-2)/TH, b = (W-2)/128, so an
+    // image has at most H*W/(128 TH) + floor(max_side/TH) + floor(max_side/128) + 3 tiles
+    const int kTileRows = ldp::variant_tile_h(0);
+    if (kTileRows < 1) return ldp::report_error(LDP_ENOTIMPL, "tile variant 0 missing");
     const uint64_t tile_bound = max_pixels / (uint64_t)(kTileRows * kTileCols) + 1 +
                                 (uint64_t)count * (uint64_t)(max_side / kTileRows + max_side / kTileCols + 3);
     const uint64_t need = 3 + (uint64_t)count + 1 + tile_bound;

@@ -28,7 +28,6 @@ namespace {
 constexpr int kRows = 64;
 constexpr int kThreads = 256;
 constexpr int kMaxCols = 4096;     // output widths whose column table fits in shared memory
-constexpr int kStatusBadCrop = 8;  // device status bit: a crop descriptor was rejected
 
 __device__ __forceinline__ void coord(int i, int n_src, int n_dst, int& i0, int& w1) {
     // y = num / den with num = (2i + 1) n_src - n_dst, den = 2 n_dst

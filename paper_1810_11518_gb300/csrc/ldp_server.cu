@@ -10,6 +10,7 @@
 // stamps the requests.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
@@ -136,6 +137,10 @@ void set_error(ldp_server* s, const std::string& msg) {
 bool launch_batch(ldp_server* s, int si) {
     ldp::Range range("ldp.server.batch");
     Slot& sl = s->slots[si];
+    if (ldp::take_fault(ldp::kFaultServerLaunch)) {  // test hook: fail before queueing anything
+        set_error(s, std::string("server batch launch (injected): ") + cudaGetErrorString(cudaErrorLaunchFailure));
+        return false;
+    }
     cudaError_t e = cudaSuccess;
     const int n = (int)sl.reqs.size();
     for (int i = 0; i < n; ++i) {
@@ -235,6 +240,11 @@ void dispatcher_main(ldp_server* s) {
         const bool ok = launch_batch(s, si);
         lk.lock();
         if (!ok) {
+            // copies already queued on the slot's stream may still read or
+            // write the batch's arena ranges: let them finish first
+            lk.unlock();
+            cudaStreamSynchronize(sl.stream);
+            lk.lock();
             for (Request& r : sl.reqs) s->arena->release(r.off, r.bytes);
             sl.reqs.clear();
             sl.busy = false;
@@ -316,7 +326,9 @@ int ldp_server_create(ldp_server** out, const ldp_server_config* cfg) {
     s->cfg = *cfg;
     s->hist_len = cfg->rs.R * cfg->rs.C * (cfg->rs.compact ? ldp_hist_bins(cfg->k) : 256);
     cudaGetDevice(&s->device);
-    cudaError_t e = cudaMalloc(&s->d_arena, cfg->arena_bytes);
+    void* arena_mem = nullptr;
+    cudaError_t e = ldp::device_malloc(&arena_mem, cfg->arena_bytes);
+    s->d_arena = static_cast<uint8_t*>(arena_mem);
     if (e != cudaSuccess) {
         cudaGetLastError();
         delete s;
@@ -334,17 +346,22 @@ int ldp_server_create(ldp_server** out, const ldp_server_config* cfg) {
         if (e == cudaSuccess) e = cudaMallocHost(&sl.h_desc, sizeof(ldp_image_desc) * cfg->max_batch);
         if (e == cudaSuccess) e = cudaMallocHost(&sl.h_count, sizeof(int));
         if (e == cudaSuccess) e = cudaMallocHost(&sl.h_hist, sizeof(uint32_t) * (size_t)s->hist_len * cfg->max_batch);
-        if (e == cudaSuccess) e = cudaMalloc(&sl.d_desc, sizeof(ldp_image_desc) * cfg->max_batch);
-        if (e == cudaSuccess) e = cudaMalloc(&sl.d_count, sizeof(int));
-        if (e == cudaSuccess) e = cudaMalloc(&sl.d_hist, sizeof(uint32_t) * (size_t)s->hist_len * cfg->max_batch);
+        if (e == cudaSuccess)
+            e = ldp::device_malloc(reinterpret_cast<void**>(&sl.d_desc), sizeof(ldp_image_desc) * cfg->max_batch);
+        if (e == cudaSuccess) e = ldp::device_malloc(reinterpret_cast<void**>(&sl.d_count), sizeof(int));
+        if (e == cudaSuccess)
+            e = ldp::device_malloc(reinterpret_cast<void**>(&sl.d_hist),
+                                   sizeof(uint32_t) * (size_t)s->hist_len * cfg->max_batch);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
         if (e == cudaSuccess) {
-            if (ldp_batch_plan_create(&sl.plan, cfg->max_batch, max_pixels, cfg->k, cfg->rs, 0) != LDP_OK) {
+            if (ldp_batch_plan_create(&sl.plan, cfg->max_batch, max_pixels, cfg->k, cfg->rs, 0) != LDP_OK ||
+                (cfg->variant >= 0 && ldp_batch_plan_set_config(sl.plan, cfg->variant, cfg->ctas_per_sm) != LDP_OK)) {
+                const std::string why = ldp_last_error();
                 destroy_resources(s);
                 delete s;
-                return LDP_ENOMEM;
+                cudaGetLastError();
+                return ldp::report_error(LDP_ENOMEM, ("server batch plan: " + why).c_str());
             }
-            if (cfg->variant >= 0) ldp_batch_plan_set_config(sl.plan, cfg->variant, cfg->ctas_per_sm);
             // short tiles: the first non-staged variant of 8-row tiles, unless a variant was fixed
             int vshort = -1;
             for (int v = 0; v < ldp::num_variants() && cfg->variant < 0; ++v) {
@@ -354,9 +371,19 @@ int ldp_server_create(ldp_server** out, const ldp_server_config* cfg) {
                     break;
                 }
             }
+            // it only runs batches of fewer than 2 x #SMs 64-row tiles; such a
+            // tile covers at most 66 x 130 input pixels, which bounds the
+            // pixels of those batches (and so the short plan's work list)
+            const uint64_t short_pixels = std::min<uint64_t>(max_pixels, 2ull * (uint64_t)s->num_sms * 66u * 130u);
             if (vshort >= 0 &&
-                ldp_batch_plan_create(&sl.plan_short, cfg->max_batch, max_pixels, cfg->k, cfg->rs, 0) == LDP_OK)
-                ldp_batch_plan_set_config(sl.plan_short, vshort, cfg->ctas_per_sm);
+                (ldp_batch_plan_create(&sl.plan_short, cfg->max_batch, short_pixels, cfg->k, cfg->rs, 0) != LDP_OK ||
+                 ldp_batch_plan_set_config(sl.plan_short, vshort, cfg->ctas_per_sm) != LDP_OK)) {
+                const std::string why = ldp_last_error();
+                destroy_resources(s);
+                delete s;
+                cudaGetLastError();
+                return ldp::report_error(LDP_ENOMEM, ("server short-tile plan: " + why).c_str());
+            }
         }
     }
     if (e != cudaSuccess) {

@@ -58,7 +58,7 @@ __device__ __forceinline__ ldp_image_desc desc_of(const CellArgs& a, int i) {
 // with a short code pitch) is skipped and sets bit 0 of the status word.
 __device__ __forceinline__ bool win_desc_ok(const ldp_image_desc& d, int max_H, int max_W, int* status) {
     const bool ok = d.H >= 3 && d.W >= 3 && d.H <= max_H && d.W <= max_W && d.code_pitch >= d.W - 2;
-    if (!ok && threadIdx.x == 0) atomicOr(status, 1);
+    if (!ok && threadIdx.x == 0) atomicOr(status, kStatusBadDesc);
     return ok;
 }
 

@@ -242,3 +242,18 @@ def test_autotune_cache_names_compiled_variants():
         assert ent["name"] == names[ent["variant"]], key
         assert ent["ctas_per_sm"] >= 0
     assert os.path.basename(autotune.DEFAULT_CACHE) == "autotune_cache.json"
+
+
+def test_fault_hook_without_gpu(lib):
+    """The test-only fault hook checks its arguments on the host; the
+    stage-wait fault exists only in the checked build."""
+    from paper_1810_11518_gb300 import _abi
+
+    assert lib.ldp_test_inject_fault(9, 0, 1, None) == _abi.LDP_EINVAL
+    assert lib.ldp_test_inject_fault(_abi.LDP_FAULT_DEVICE_ALLOC, -1, 1, None) == _abi.LDP_EINVAL
+    assert lib.ldp_test_inject_fault(_abi.LDP_FAULT_SERVER_LAUNCH, 0, -1, None) == _abi.LDP_EINVAL
+    assert lib.ldp_test_inject_fault(_abi.LDP_FAULT_STAGE_WAIT, 0, 1, None) == _abi.LDP_ENOTIMPL
+    assert lib.ldp_test_inject_fault(_abi.LDP_FAULT_STAGE_WAIT, 1, 1, None) == _abi.LDP_EINVAL
+    for kind in (_abi.LDP_FAULT_DEVICE_ALLOC, _abi.LDP_FAULT_SERVER_LAUNCH):
+        assert lib.ldp_test_inject_fault(kind, 2, 1, None) == 0
+        assert lib.ldp_test_inject_fault(kind, 0, 0, None) == 0  # cleared again

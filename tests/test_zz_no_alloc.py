@@ -1,6 +1,7 @@
 """The allocation-free batch entry point (ldp_batch_run_noalloc), called
-through the C-ABI and checked against the regular plan-based batch run on
-the same inputs, on two calls in a row.
+through the C-ABI and checked against the regular plan-based batch run and
+the CPU oracle (Eqs. 1-6, bit for bit) on the same inputs, on two calls in a
+row.
 
 It exists for callers that cannot allocate device memory while they run:
 memory budgeted once at start-up, or owned by another allocator's pool, or
@@ -41,7 +42,7 @@ def _batch(env, seeds, lo, hi, k):
     host = np.zeros(lay.img_bytes, dtype=np.uint8)
     synth.batch_into(host, seeds, Hs, Ws, lay.pitches, lay.img_off)
     d_img = torch.from_numpy(host).cuda()
-    return lay, d_img, max(max(Hs), max(Ws))
+    return lay, host, d_img, max(max(Hs), max(Ws))
 
 
 def _run_both(env, lay, d_img, max_side, k):
@@ -68,14 +69,21 @@ def _run_both(env, lay, d_img, max_side, k):
 
 
 def test_noalloc_matches_plan_run_twice(env):
+    import oracle
+
     torch, ldp, synth, _abi = env
     # first call: 24 uneven images; second call: a different, smaller batch
     # with another k, so the shared array holds the first call's leftovers
     for seeds, lo, hi, k in ((list(range(3000, 3024)), 3, 400, 3), (list(range(3100, 3107)), 30, 260, 2)):
-        lay, d_img, max_side = _batch(env, seeds, lo, hi, k)
+        lay, host, d_img, max_side = _batch(env, seeds, lo, hi, k)
         (c_ref, h_ref), (c_na, h_na) = _run_both(env, lay, d_img, max_side, k)
         for i in range(lay.n):  # compare inside each code rectangle, tolerance 0
             assert np.array_equal(lay.codes(c_na, i), lay.codes(c_ref, i)), i
+            # and against the oracle, image by image
+            ho, co = oracle.extract(lay.image(host, i), k=k, R=7, C=6, compact=True, W=int(lay.Ws[i]))
+            assert np.array_equal(lay.codes(c_na, i), co), i
+            assert np.array_equal(h_na[i * lay.hist_len:(i + 1) * lay.hist_len].astype(np.uint32),
+                                  ho.reshape(-1)), i
         assert np.array_equal(h_na, h_ref)
         assert (h_ref.reshape(lay.n, -1).sum(axis=1) == (lay.Hs - 2) * (lay.Ws - 2)).all()
     assert ldp.device_status() == 0
