@@ -59,8 +59,9 @@ def parse():
     ap.add_argument("--ctas-per-sm", type=int, default=0)
     ap.add_argument("--cpu-sample", type=int, default=2048, help="images in the oracle CPU sample")
     ap.add_argument("--no-extras", action="store_true", help="skip plain / LBP / serving / CPU legs")
-    ap.add_argument("--serve-seconds", type=float, default=2.0, help="measured seconds per serving rate")
-    ap.add_argument("--large", action="store_true", help="also time 64 images of 8192x8192, k = 1..4")
+    ap.add_argument("--serve-seconds", type=float, default=10.0, help="measured seconds per serving rate")
+    ap.add_argument("--serve-warmup", type=float, default=2.0, help="warm-up seconds per serving rate")
+    ap.add_argument("--no-large", action="store_true", help="skip the 64 x 8192x8192, k = 1..4 leg")
     ap.add_argument("--e2e-chunk", type=int, default=128, help="images per chunk of the end-to-end pipeline")
     ap.add_argument("--e2e-nbuf", type=int, default=3, help="device buffers / streams of the end-to-end pipeline")
     return ap.parse_args()
@@ -212,6 +213,168 @@ def cpu_oracle_sample(n_images, H, W, k, threads=None, min_seconds=10.0, max_pas
         dt += time.perf_counter() - t0
         passes += 1
     return passes * n_images * H * W / dt / 1e6, dt, threads, passes
+
+
+def host_cpu():
+    """Model name and logical core count of this host (lscpu, else /proc/cpuinfo)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().lower().startswith("model name"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for ln in f:
+                    if ln.lower().startswith(("model name", "cpu part")):
+                        model = ln.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    import platform
+
+    return {"model": model or platform.processor() or "unknown", "arch": platform.machine(),
+            "logical_cores": os.cpu_count()}
+
+
+# The paper's Table 2 (Sec. 4.1): LDP over ALDP running time, 1..10 images,
+# Python on an Intel i5-3230M (2.6 GHz): 11.04/2.81 .. 106.67/26.95 s.
+PAPER_ALDP_SPEEDUP = {"min": 3.79, "max": 3.96, "hardware": "Intel Core i5-3230M 2.6 GHz, Python (Sec. 3.3)",
+                      "source": "Table 2, Sec. 4.1"}
+
+
+def _timed(fn, min_s):
+    """Calls fn() until min_s seconds have passed (at least once); seconds per call."""
+    n, t0 = 0, time.perf_counter()
+    while True:
+        fn()
+        n += 1
+        dt = time.perf_counter() - t0
+        if dt >= min_s:
+            return dt / n
+
+
+def cpu_baselines(H, W, k, min_s=0.5):
+    """The paper's scheme and the oracle on this host's cores: LDP codes +
+    region histograms along three response routes (literal masks = the
+    oracle, the paper's column sums of Eqs. 7-29, the ring-sum identity), all
+    ending in the same code step and histograms, from an -O3 build of the
+    unchanged oracle sources.  Config 1 (one 640x490 image, seed 0, 256-bin
+    whole-image histogram) single-threaded; a config-2 sample (7x6 regions,
+    56 bins) single-threaded and one thread per core; and the responses
+    alone (the part Sec. 2.3 accelerates), single-threaded."""
+    import oracle
+    import synth
+
+    thr = max(1, os.cpu_count() or 1)
+    oracle.build(timed=True)  # compiled before anything is timed
+    routes = {"oracle_masks": oracle.ROUTE_MASKS, "aldp": oracle.ROUTE_ALDP, "ring_sums": oracle.ROUTE_RINGSUM}
+    one = np.ascontiguousarray(synth.image(0, H, W, 3.0)).reshape(-1)
+    off1 = np.zeros(1, dtype=np.int64)
+    n1, nall = 8, 8 * thr
+    many = np.ascontiguousarray(synth.batch(list(range(nall)), H, W, 3.0, threads=thr)).reshape(-1)
+    offs = np.arange(nall, dtype=np.int64) * (H * W)
+    entries = []
+    ref = None
+    for name, r in routes.items():
+        oracle.route_extract_batch(r, one, off1, H, W, W, k=k, R=1, C=1, compact=False, threads=1, timed=True)
+        s1 = _timed(lambda: oracle.route_extract_batch(r, one, off1, H, W, W, k=k, R=1, C=1, compact=False,
+                                                       threads=1, timed=True), min_s)
+        entries.append({"route": name, "kind": oracle.ROUTE_NAMES[r], "workload": f"1 x {W}x{H} (config 1)",
+                        "work": "codes + 256-bin whole-image histogram", "threads": 1,
+                        "value": round(H * W / s1 / 1e6, 3), "unit": UNIT, "us_per_image": round(s1 * 1e6, 1)})
+        for nimg, t in ((n1, 1), (nall, thr)):
+            sec = _timed(lambda: oracle.route_extract_batch(r, many, offs[:nimg], H, W, W, k=k, R=7, C=6,
+                                                            compact=True, threads=t, timed=True), min_s)
+            entries.append({"route": name, "kind": oracle.ROUTE_NAMES[r],
+                            "workload": f"{nimg} x {W}x{H} (config 2 sample, seeds 0..{nimg - 1})",
+                            "work": "codes + 7x6 region histograms (56 bins)", "threads": t,
+                            "value": round(nimg * H * W / sec / 1e6, 3), "unit": UNIT})
+        rs = _timed(lambda: oracle.route_response_sum(r, one, off1, H, W, W, timed=True), min_s)
+        entries.append({"route": name, "kind": oracle.ROUTE_NAMES[r], "workload": f"1 x {W}x{H} (config 1)",
+                        "work": "the eight responses only (no code step)", "threads": 1,
+                        "value": round(H * W / rs / 1e6, 3), "unit": UNIT})
+        h = oracle.route_extract_batch(r, many, offs[:n1], H, W, W, k=k, R=7, C=6, threads=thr, timed=True)
+        ref = h if ref is None else ref
+        if not np.array_equal(h, ref):
+            raise RuntimeError(f"CPU route {name} disagrees with the oracle route")
+
+    def val(route, work, threads):
+        return next(e["value"] for e in entries
+                    if e["route"] == route and e["work"].startswith(work) and e["threads"] == threads)
+
+    ratios = {
+        "aldp_over_masks_codes_hist_1_thread": round(val("aldp", "codes + 7x6", 1) / val("oracle_masks", "codes + 7x6", 1), 3),
+        "aldp_over_masks_codes_hist_all_cores": round(val("aldp", "codes + 7x6", thr) / val("oracle_masks", "codes + 7x6", thr), 3),
+        "aldp_over_masks_responses_only": round(val("aldp", "the eight", 1) / val("oracle_masks", "the eight", 1), 3),
+        "paper_table2_ldp_over_aldp": PAPER_ALDP_SPEEDUP,
+    }
+    return {"host": host_cpu(), "build": "gcc -O3 -flto of the unchanged oracle sources (no -march: the same "
+                                          "build on every host)",
+            "entries": entries, "ratios": ratios}
+
+
+def time_single_image(ldp, torch, dev, H, W, k, reps=300):
+    """Config 1: one 640x490 image (seed 0), k=3 codes + one 256-bin
+    whole-image histogram through one ldp_region_hist C-ABI call (histogram
+    zeroing + fused kernel).  Device latency: CUDA events around each call,
+    median over `reps` calls.  Host to host: pinned image in, the call, codes
+    and histogram back, stream synchronised; median wall time."""
+    import synth
+    from paper_1810_11518_gb300 import _abi
+
+    img = synth.image(0, H, W, 3.0)
+    h_img = torch.from_numpy(img).pin_memory()
+    d_img = h_img.to(dev)
+    d_codes = torch.empty((H - 2, W - 2), dtype=torch.uint8, device=dev)
+    d_hist = torch.empty(256, dtype=torch.int32, device=dev)
+    h_codes = torch.empty((H - 2, W - 2), dtype=torch.uint8, pin_memory=True)
+    h_hist = torch.empty(256, dtype=torch.int32, pin_memory=True)
+    lib = _abi.load()
+    stream = torch.cuda.current_stream(dev)
+    sptr = ctypes.c_void_p(stream.cuda_stream)
+    args = (ctypes.c_void_p(d_img.data_ptr()), H, W, W, k, _abi.RegionSpec(1, 1, 0), ctypes.c_void_p(d_hist.data_ptr()),
+            ctypes.c_void_p(d_codes.data_ptr()), W - 2, sptr)
+    ldp.set_plain_variant(-1)
+
+    def call():
+        rc = lib.ldp_region_hist(*args)
+        if rc:
+            _abi.check(rc, "ldp_region_hist")
+
+    for _ in range(20):
+        call()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    torch.cuda.synchronize(dev)
+    for e0, e1 in ev:
+        e0.record(stream)
+        call()
+        e1.record(stream)
+    torch.cuda.synchronize(dev)
+    dev_us = statistics.median(e0.elapsed_time(e1) * 1e3 for e0, e1 in ev)
+    host_us = []
+    for i in range(reps + 10):
+        t0 = time.perf_counter()
+        d_img.copy_(h_img, non_blocking=True)
+        call()
+        h_codes.copy_(d_codes, non_blocking=True)
+        h_hist.copy_(d_hist, non_blocking=True)
+        stream.synchronize()
+        if i >= 10:
+            host_us.append((time.perf_counter() - t0) * 1e6)
+    h2h_us = statistics.median(host_us)
+    ok = int(h_hist.sum().item()) == (H - 2) * (W - 2)
+    return {"workload": f"1 x {W}x{H} uint8 (seed 0), k={k} codes + 256-bin whole-image histogram",
+            "device_us": round(dev_us, 2), "value": round(H * W / (dev_us * 1e-6) / 1e6, 3), "unit": UNIT,
+            "host_to_host_us": round(h2h_us, 2),
+            "host_to_host_value": round(H * W / (h2h_us * 1e-6) / 1e6, 3), "calls": reps,
+            "launches_per_call": 2, "hist_mass_ok": ok,
+            "note": "median of CUDA-event latencies around single ldp_region_hist calls (histogram zeroing + "
+                    "kernel); host to host adds the pinned H2D of the image and the D2H of codes and histogram"}
 
 
 def time_batch(ldp, torch, dev, Hs, Ws, seeds, ks, regions, sigma, steps, tune=True):
@@ -686,21 +849,33 @@ def main():
             time_windows(ldp, torch, dev, n, 260, 260, k, (20, 20), None, max(5, a.steps // 10), peak),
             time_windows(ldp, torch, dev, n, H, W, k, (20, 20), (10, 10), max(5, a.steps // 10), peak),
         ]
-    if a.large and rank == 0:
+    if not a.no_extras and rank == 0:
+        # ---- config 1: one 640x490 image through the plain entry point ----
+        extras["single_image"] = time_single_image(ldp, torch, dev, H, W, k)
+    if not a.no_extras and not a.no_large and rank == 0:
         # ---- large images: 64 x 8192^2 (sigma 6), 16x16 regions, k = 1..4 ----
-        extras["large_batched"] = time_batch(ldp, torch, dev, [8192] * 64, [8192] * 64, np.arange(64), (1, 2, 3, 4),
-                                             (16, 16), 6.0, 5)
+        large = time_batch(ldp, torch, dev, [8192] * 64, [8192] * 64, np.arange(64), (1, 2, 3, 4), (16, 16), 6.0, 5)
+        for e in large:
+            e["hbm_frac"] = round(e["achieved_gbs"] / peak, 4)
+        extras["large_batched"] = large
 
     if not a.no_extras and rank == 0 and a.serve_seconds > 0:
-        # ---- continuous-batching serving (Poisson arrivals, uneven 64..1024 sizes) ----
+        # ---- continuous-batching serving (Poisson arrivals): sizes uniform on
+        # [64, 1024]^2 and fixed 640x490 requests ----
         from paper_1810_11518_gb300 import serving
 
-        pool = serving.RequestPool(512, "uneven")
         extras["serving"] = []
-        for rate in (5000, 20000, 50000):
-            with serving.Server(streams=3, max_batch=256, arena_bytes=1 << 30) as srv:
-                res = serving.run_load(srv, pool, rate, a.serve_seconds, warmup=0.5, seed=rate)
-            extras["serving"].append({kk: (round(vv, 4) if isinstance(vv, float) else vv) for kk, vv in res.items()})
+        for dist in ("uneven", "faces"):
+            pool = serving.RequestPool(512, dist)
+            for rate in (5000, 20000, 50000):
+                with serving.Server(streams=3, max_batch=256, arena_bytes=1 << 30) as srv:
+                    res = serving.run_load(srv, pool, rate, a.serve_seconds, warmup=a.serve_warmup, seed=rate)
+                res = {kk: (round(vv, 4) if isinstance(vv, float) else vv) for kk, vv in res.items()}
+                res["sizes"] = "H, W uniform on [64, 1024]" if dist == "uneven" else "640x490"
+                res["window_s"] = a.serve_seconds
+                res["warmup_s"] = a.serve_warmup
+                extras["serving"].append(res)
+            del pool
 
 
     # ---- correctness spot check of the timed output (cheap): masses ----
@@ -713,6 +888,7 @@ def main():
         cpu = {"value": round(v, 3), "unit": UNIT, "cores": thr, "kind": "oracle",
                "sample": f"{min(a.cpu_sample, n)} of the {n} images (seeds 0..{min(a.cpu_sample, n) - 1}), "
                          f"codes + 7x6 hist, {passes} pass(es), {dt:.1f} s"}
+        extras["cpu_baselines"] = cpu_baselines(H, W, k)
 
     if rank == 0:
         line = {

@@ -20,11 +20,20 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRCS = [os.path.join(_HERE, f) for f in ("oracle_ldp.c", "aldp.c")]
+_SRCS = [os.path.join(_HERE, f) for f in ("oracle_ldp.c", "aldp.c", "cpu_routes.c")]
 _HDR = os.path.join(_HERE, "oracle_ldp.h")
 _LIB = os.path.join(_HERE, "_oracle.so")
+# the same sources built -O3 with link-time inlining across them, for the
+# timed CPU baselines only (the sources are unchanged; no -march, so the
+# build is the same on every host)
+_LIB_TIMED = os.path.join(_HERE, "_oracle_o3.so")
 _lock = threading.Lock()
 _lib = None
+_lib_timed = None
+
+ROUTE_MASKS, ROUTE_ALDP, ROUTE_RINGSUM = 0, 1, 2
+ROUTE_NAMES = {ROUTE_MASKS: "literal masks (Eq. 1)", ROUTE_ALDP: "paper's column sums (Eqs. 7-29)",
+               ROUTE_RINGSUM: "ring sums (m_i = 8 S3_i - 3 S8)"}
 
 MODE_LDP = 0
 MODE_LBP = 1
@@ -33,15 +42,17 @@ MODE_LDP_THRESH = 3      # rank by |m_i|, every bit tied with the k-th set
 MODE_LDP_RAW_THRESH = 4  # rank by m_i, every bit tied with the k-th set
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle into oracle/_oracle.so (plain C, -O2, no -march)."""
+def build(force: bool = False, timed: bool = False) -> str:
+    """Compile the oracle into oracle/_oracle.so (plain C, -O2, no -march);
+    timed=True: the same sources into oracle/_oracle_o3.so with -O3 -flto,
+    the build the CPU baselines are timed on."""
+    lib, flags = (_LIB_TIMED, ["-O3", "-flto"]) if timed else (_LIB, ["-O2"])
     newest = max(os.path.getmtime(p) for p in _SRCS + [_HDR])
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
-        tmp = _LIB + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-pthread",
-                               "-o", tmp] + _SRCS)
-        os.replace(tmp, _LIB)
-    return _LIB
+    if force or not os.path.exists(lib) or os.path.getmtime(lib) < newest:
+        tmp = lib + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc"] + flags + ["-std=c11", "-fPIC", "-shared", "-pthread", "-o", tmp] + _SRCS)
+        os.replace(tmp, lib)
+    return lib
 
 
 def _load():
@@ -75,8 +86,24 @@ def _load():
             lib.oracle_resize_coord.restype = None
             lib.oracle_hist_distance.argtypes = [vp, i32, i32, vp, i32, i32, i32, i32, vp, i32]
             lib.oracle_window_hist.argtypes = [vp, i32, i32, i32, i32, i32, i32, i32, i32, vp]
+            lib.route_extract_batch.argtypes = [i32, i32, vp, vp, i32, i32, i32, i32, i32, i32, i32, vp, i32]
+            lib.route_response_sum.argtypes = [i32, i32, vp, vp, i32, i32, i32]
+            lib.route_response_sum.restype = ctypes.c_int64
             _lib = lib
     return _lib
+
+
+def _load_timed():
+    global _lib_timed
+    with _lock:
+        if _lib_timed is None:
+            lib = ctypes.CDLL(build(timed=True))
+            lib.route_extract_batch.argtypes = [ctypes.c_int] * 2 + [ctypes.c_void_p] * 2 + [ctypes.c_int] * 7 + \
+                                               [ctypes.c_void_p, ctypes.c_int]
+            lib.route_response_sum.argtypes = [ctypes.c_int] * 2 + [ctypes.c_void_p] * 2 + [ctypes.c_int] * 3
+            lib.route_response_sum.restype = ctypes.c_int64
+            _lib_timed = lib
+    return _lib_timed
 
 
 def _u8(img: np.ndarray) -> np.ndarray:
@@ -317,3 +344,29 @@ def extract_batch(buf: np.ndarray, img_off, Hs, Ws, pitches, k: int = 3, R: int 
         maps = [code_buf[code_off[i]:code_off[i] + (Hs[i] - 2) * (Ws[i] - 2)].reshape(Hs[i] - 2, Ws[i] - 2)
                 for i in range(n)]
     return hist, maps
+
+
+def route_extract_batch(route: int, buf: np.ndarray, img_off, H: int, W: int, pitch: int, k: int = 3, R: int = 7,
+                        C: int = 6, compact: bool = True, threads: int = 1, timed: bool = False) -> np.ndarray:
+    """Region histograms (n, R, C, bins) of n H x W images of one flat buffer
+    along one response route (ROUTE_MASKS / ROUTE_ALDP / ROUTE_RINGSUM), all
+    ending in the oracle's code step and histograms.  timed=True runs the -O3
+    build the CPU baselines are timed on."""
+    n = len(img_off)
+    img_off = np.ascontiguousarray(img_off, dtype=np.int64)
+    hist = np.zeros((n, R, C, nbins(MODE_LDP, k, compact)), dtype=np.uint32)
+    lib = _load_timed() if timed else _load()
+    rc = lib.route_extract_batch(int(route), n, buf.ctypes.data, img_off.ctypes.data, H, W, pitch, k, R, C,
+                                 int(compact), hist.ctypes.data, int(threads))
+    if rc:
+        raise ValueError("route_extract_batch rejected the arguments")
+    return hist
+
+
+def route_response_sum(route: int, buf: np.ndarray, img_off, H: int, W: int, pitch: int,
+                       timed: bool = False) -> int:
+    """Sum of |m_i| over every interior pixel and direction of n images, with
+    the responses of one route only (no code step), single-threaded."""
+    img_off = np.ascontiguousarray(img_off, dtype=np.int64)
+    lib = _load_timed() if timed else _load()
+    return int(lib.route_response_sum(int(route), len(img_off), buf.ctypes.data, img_off.ctypes.data, H, W, pitch))

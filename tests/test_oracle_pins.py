@@ -279,3 +279,24 @@ def test_rejects_bad_arguments(orc):
         orc.codes(np.zeros((4, 4), np.uint8), k=0)
     with pytest.raises(ValueError):
         orc.codes(np.zeros((4, 4), np.uint8), k=8)
+
+
+def test_timed_cpu_routes_equal_the_oracle(orc):
+    """The driver bench.py times (three response routes, the same code step
+    and histograms) gives the oracle's histograms on every route, in both
+    builds, raw and compact, on several threads; the responses alone agree."""
+    import synth
+
+    imgs = synth.batch(list(range(5)), 37, 53, 3.0)
+    flat = np.ascontiguousarray(imgs.reshape(-1))
+    offs = np.arange(5, dtype=np.int64) * (37 * 53)
+    for R, C, compact, k in ((7, 6, True, 3), (1, 1, False, 2)):
+        ref, _ = orc.extract_batch(flat, offs, [37] * 5, [53] * 5, [53] * 5, k=k, R=R, C=C, compact=compact)
+        for route in (orc.ROUTE_MASKS, orc.ROUTE_ALDP, orc.ROUTE_RINGSUM):
+            for timed in (False, True):
+                got = orc.route_extract_batch(route, flat, offs, 37, 53, 53, k=k, R=R, C=C, compact=compact,
+                                              threads=3, timed=timed)
+                assert np.array_equal(got, ref), (route, timed)
+    sums = {orc.route_response_sum(r, flat, offs, 37, 53, 53, timed=t) for r in range(3) for t in (False, True)}
+    m = sum(np.abs(orc.responses(imgs[i], x, y)).sum() for i in range(5) for x in range(1, 36) for y in range(1, 52))
+    assert sums == {int(m)}
