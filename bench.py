@@ -400,11 +400,14 @@ def time_batch(ldp, torch, dev, Hs, Ws, seeds, ks, regions, sigma, steps, tune=T
         with ldp.BatchPlan(lay.n, lay.pixels, k=k, regions=regions) as plan:
             props = torch.cuda.get_device_properties(dev)
             ent = autotune.lookup(torch.cuda.get_device_name(dev), props.multi_processor_count, "batch", k,
-                                  "hist+codes", lay.pixels / lay.n)
+                                  "hist+codes", lay.pixels / lay.n, mixed=len(set(zip(Hs, Ws))) > 1)
+            vname, how = ldp.variant_name(0), "default"
             if ent:
                 plan.set_config(ent["variant"], ent["ctas_per_sm"])
+                vname, how = ent["name"], "cache"
             elif tune:
-                autotune.tune_plan(plan, d_desc, d_count, d_hist, reps=3, warmup=1)
+                vname = autotune.tune_plan(plan, d_desc, d_count, d_hist, reps=3, warmup=1)["name"]
+                how = "tuned on the fly"
             for _ in range(3):
                 plan.run(d_desc, d_count, d_hist)
             plan.enable_timing(steps)
@@ -420,7 +423,8 @@ def time_batch(ldp, torch, dev, Hs, Ws, seeds, ks, regions, sigma, steps, tune=T
         alg = algorithmic_bytes(lay.Hs, lay.Ws, hist_len)
         out.append({"images": lay.n, "pixels": lay.pixels, "k": k, "regions": list(regions),
                     "ms_per_step": round(ms, 4), "value": round(lay.pixels / (ms * 1e-3) / 1e6, 3), "unit": UNIT,
-                    "kernel_ms": round(kms, 4), "achieved_gbs": round(alg / (kms * 1e-3) / 1e9, 1)})
+                    "kernel_ms": round(kms, 4), "achieved_gbs": round(alg / (kms * 1e-3) / 1e9, 1),
+                    "variant": vname, "variant_from": how})
     return out
 
 

@@ -301,7 +301,9 @@ LDP_API int ldp_num_variants(void);
 /* Short description of a variant, static storage: "r<rows per warp tile>
  * w<warps per CTA> b<min CTAs per SM> t<1: rows staged by the bulk-copy
  * engine>" and a trailing "s" when a tile narrower than 64 columns shares
- * its rows among lane groups (e.g. "r128w4b7t0", "r64w4b7t0s"). */
+ * its rows among lane groups, or "f" when the shared histogram slots hold
+ * the current region row only and are flushed at each region-row boundary
+ * (e.g. "r128w4b7t0", "r64w4b7t0s", "r128w4b6t0f"). */
 LDP_API const char *ldp_variant_name(int variant);
 /* Variant used by the single-image entry points; -1 (the default) chooses
  * by image size: short warp tiles for images of few 64-row tiles (their

@@ -34,8 +34,11 @@ def size_class(pixels_per_image: float) -> str:
     return "large"
 
 
-def make_key(device: str, sms: int, path: str, k: int, mode: str, pixels_per_image: float) -> str:
-    return f"{device}|{sms}|{path}|k{k}|{mode}|{size_class(pixels_per_image)}"
+def make_key(device: str, sms: int, path: str, k: int, mode: str, pixels_per_image: float,
+             mixed: bool = False) -> str:
+    """Cache key; batches of images of different sizes (mixed) are tuned
+    apart from batches of one size in the same size class."""
+    return f"{device}|{sms}|{path}|k{k}|{mode}|{size_class(pixels_per_image)}" + ("|mixed" if mixed else "")
 
 
 def load_cache(path: str | None = None) -> dict:
@@ -47,10 +50,10 @@ def load_cache(path: str | None = None) -> dict:
 
 
 def lookup(device: str, sms: int, path: str, k: int, mode: str, pixels_per_image: float,
-           cache: dict | None = None) -> dict | None:
+           cache: dict | None = None, mixed: bool = False) -> dict | None:
     """The cached {"variant", "ctas_per_sm", ...} for this workload, or None."""
     c = load_cache() if cache is None else cache
-    return c.get(make_key(device, sms, path, k, mode, pixels_per_image))
+    return c.get(make_key(device, sms, path, k, mode, pixels_per_image, mixed))
 
 
 def tune_plan(plan, d_desc, d_count, d_hist, ctas_options=(0, 4), reps: int = 8, warmup: int = 2) -> dict:
@@ -124,7 +127,7 @@ def _tune_workload(name, Hs, Ws, seeds, k, lbp, sigma, out, hist=True):
         res = tune_plan(plan, d_desc, d_count, d_hist if hist else None)
     mode = ("lbp+" if lbp else "") + ("hist+codes" if hist else "codes")
     key = make_key(torch.cuda.get_device_name(0), dev.multi_processor_count, "batch", k if not lbp else 0, mode,
-                   lay.pixels / lay.n)
+                   lay.pixels / lay.n, mixed=len(set(zip(Hs, Ws))) > 1)
     store(key, res, out)
     print(key, res["name"], res["ctas_per_sm"], f"{res['kernel_ms']:.4f} ms", flush=True)
 
@@ -142,10 +145,9 @@ def main():
 
     n = a.images
     seeds = list(range(n))
-    # uneven 64..1024 (same size class as the faces, tuned first so the
-    # 640x490 entries below take precedence), 640x490 faces (LDP k = 1..4 and
-    # LBP), 260x260 face crops (codes only, the front end's extraction),
-    # 8192^2 stress
+    # uneven 64..1024 (a "mixed" entry of the faces' size class), 640x490
+    # faces (LDP k = 1..4 and LBP), 260x260 face crops (codes only, the front
+    # end's extraction), 8192^2 stress
     sizes = [synth.sizes(s) for s in range(n)]
     _tune_workload("uneven", [h for h, _ in sizes], [w for _, w in sizes], seeds, 3, False, 3.0, a.out)
     for k in (3, 1, 2, 4):

@@ -34,7 +34,8 @@ def nvcc() -> str:
 
 
 def variants() -> list[tuple[int, int, int, int, int, int]]:
-    """(id, rows per tile, warps per CTA, min CTAs per SM, staged, split) of every tile variant."""
+    """(id, rows per tile, warps per CTA, min CTAs per SM, staged, split) of every tile variant
+    (split: 1 = narrow tiles split their rows, 2 = histogram slots per region row)."""
     with open(os.path.join(CSRC, "ldp_launch.h")) as f:
         src = f.read()
     m = re.search(r"#define LDP_VARIANTS\(X\)((?:.*\\\n)*.*)", src)

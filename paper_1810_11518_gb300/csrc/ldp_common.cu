@@ -30,7 +30,10 @@ int* status_word() {
     return addr[dev];
 }
 
-#define LDP_NAME(ID, RPW, NW, MB, ST, SP) (SP ? "r" #RPW "w" #NW "b" #MB "t" #ST "s" : "r" #RPW "w" #NW "b" #MB "t" #ST),
+#define LDP_NAME(ID, RPW, NW, MB, ST, SP)                                \
+    (SP == 1   ? "r" #RPW "w" #NW "b" #MB "t" #ST "s"                   \
+     : SP == 2 ? "r" #RPW "w" #NW "b" #MB "t" #ST "f"                   \
+               : "r" #RPW "w" #NW "b" #MB "t" #ST),
 #define LDP_TH(ID, RPW, NW, MB, ST, SP) (RPW),
 #define LDP_COUNT(ID, RPW, NW, MB, ST, SP) +1
 static const char* kVariantNames[] = {LDP_VARIANTS(LDP_NAME)};

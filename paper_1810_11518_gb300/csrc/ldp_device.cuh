@@ -412,19 +412,66 @@ __device__ __forceinline__ int band_lo(int b, int n, int nb) {
     return (int)(((uint64_t)b * (uint64_t)n) / (uint64_t)nb);
 }
 
+// Flush of a warp's shared histogram slots [0, nsl): slot sl holds region
+// row ri_first + sl / ncs, region column rj_lo + sl % ncs.  Every non-zero
+// bin of a code that can occur is added to the global histogram and reset
+// (the C(8,k) codes with popcount k for the exact-k LDP modes, bin = position
+// in the code list when compact, the code itself when raw; every code but 0
+// for the LDP threshold modes, whose code 0 holds the skipped columns; all
+// 256 for LBP).  Warp-collective.
+template <int MODE, int K>
+__device__ __forceinline__ void flush_slots(const Job& jb, const HistCfg& hc, uint32_t* wh, int ri_first,
+                                            int rj_lo, int ncs, int nsl, int* status) {
+    const int lane = threadIdx.x & 31;
+    asm volatile("" ::: "memory");  // the reductions into wh come first
+    __syncwarp();
+    constexpr int NC = exact_k(MODE) ? binom_ce(8, K) : 256;
+    constexpr int NI = (NC + 31) / 32;
+    int code_of[NI];
+#pragma unroll
+    for (int m = 0; m < NI; ++m) {
+        const int idx = lane + 32 * m;
+        code_of[m] = exact_k(MODE) ? (idx < NC ? (int)__ldg(&g_code_list.code[K][idx]) : -1)
+                                   : ((is_ldp(MODE) && idx == 0) ? -1 : idx);
+    }
+    for (int sl = 0; sl < nsl; ++sl) {
+        const int hbase = ((ri_first + sl / ncs) * hc.C + rj_lo + sl % ncs) * hc.nbins;
+        uint32_t* hs = wh + sl * 256;
+#pragma unroll
+        for (int m = 0; m < NI; ++m) {
+            const int code = code_of[m];
+            if (code >= 0) {
+                const uint32_t c = hs[code];
+                if (c) {
+                    const int bin = (exact_k(MODE) && hc.compact) ? lane + 32 * m : code;
+                    if (index_ok(hbase + bin < hc.R * hc.C * hc.nbins, status)) atomicAdd(&jb.hist[hbase + bin], c);
+                    hs[code] = 0;
+                }
+            }
+        }
+    }
+    __syncwarp();
+}
+
 // One warp processes one tile of RW output rows x 128 output columns at
 // (u0, v0): lane l owns columns v0+4l .. v0+4l+3 and walks down the rows.
 // Input rows come either from per-lane global loads one row ahead, or
 // (STAGED, for 16-byte aligned images) from the warp's bulk-copy ring, two
 // stages ahead.  With HIST the codes are counted in the warp's private shared
-// histogram `wh` (kWarpSlots x 256 raw bins; every bin the flush reads is
-// zero on entry and on exit): the flush adds every non-zero bin to the global
-// histogram and resets it.  In the LDP modes bin 0 of a slot (code 0, which
+// histogram `wh` (kWarpSlots x 256 raw bins, one slot per region the counts
+// go to; every bin the flush reads is zero on entry and on exit): the flush
+// adds every non-zero bin to the global histogram and resets it.  A slot per
+// (region row, region column) of the tile is kept until the tile ends; with
+// RSLOTS (per-lane loads, neither STAGED nor SPLIT) the slots hold the
+// region columns of the current region row only: the rows are walked in
+// segments that end at region-row boundaries and the slots are flushed
+// there, so a tile that crosses many region rows of a small image still
+// counts in shared memory.  In the LDP modes bin 0 of a slot (code 0, which
 // they never produce) takes the counts of columns past the interior and is
 // never read; LBP has a junk slot for them.
 // Region grids too fine for kWarpSlots slots count straight into global
 // memory.  `ph` holds the ring's per-stage wait parities across tiles.
-template <int MODE, int K, int RW, bool HIST, bool STAGED, bool SPLIT>
+template <int MODE, int K, int RW, bool HIST, bool STAGED, bool SPLIT, bool RSLOTS>
 __device__ __forceinline__ void warp_tile(const Job& jb, const HistCfg& hc, int u0, int v0, uint32_t* wh,
                                           WarpRing* ring, uint32_t& ph, int* status) {
     const int lane = threadIdx.x & 31;
@@ -446,6 +493,9 @@ __device__ __forceinline__ void warp_tile(const Job& jb, const HistCfg& hc, int 
         }
     }
     const int v = v0 + 4 * lc;
+    // slots per region column of the current region row, flushed at each
+    // region-row boundary (else: per region of the tile, flushed at its end)
+    constexpr bool kRowSlots = RSLOTS && !STAGED && !SPLIT;
 
     // region slots of the tile (uniform across the warp)
     int ri_lo = 0, rj_lo = 0, ncs = 1, nslots = 1;
@@ -454,7 +504,7 @@ __device__ __forceinline__ void warp_tile(const Job& jb, const HistCfg& hc, int 
         ri_lo = band_of(u0 + 1, H, hc.R);
         rj_lo = band_of(v0 + 1, W, hc.C);
         ncs = band_of(min(v0 + kTileW, W - 2), W, hc.C) - rj_lo + 1;
-        nslots = (band_of(ue, H, hc.R) - ri_lo + 1) * ncs;
+        nslots = kRowSlots ? ncs : (band_of(ue, H, hc.R) - ri_lo + 1) * ncs;
         use_smem = nslots <= kWarpSlots;
     }
 
@@ -528,13 +578,15 @@ __device__ __forceinline__ void warp_tile(const Job& jb, const HistCfg& hc, int 
                     if (valid[t]) cp[t] = (uint8_t)(packed >> (8 * t));
             }
         }
-        if constexpr (HIST) {
+        if constexpr (HIST && !kRowSlots) {
             while (u + 1 >= next_b) {  // crossed into the next region row
                 ++ri;
                 next_b = band_lo(ri + 1, H, hc.R);
                 rowb = use_smem ? (ri - ri_lo) * ncs * 256 : ri * hc.C;
                 if (use_smem) set_sbase();
             }
+        }
+        if constexpr (HIST) {
             if (use_smem && is_ldp(MODE)) {
                 // LDP codes spread over the bins: one byte extract, one
                 // multiply-add for the address, one reduction per pixel
@@ -675,6 +727,71 @@ __device__ __forceinline__ void warp_tile(const Job& jb, const HistCfg& hc, int 
                     if (done) ph ^= 1u << sidx;
                 }
         }
+    } else if constexpr (kRowSlots) {  // per-lane global loads, one row ahead, in region-row segments
+        // every lane walks the rows (lanes past the interior count into
+        // bins the flush never reads), in segments of one region row
+        const uint8_t* rp = jb.img + (size_t)u0 * P;
+        const uint8_t* pf = rp + 3 * P;  // next input row to prefetch (one row ahead)
+        Raw nx = load_raw(rp + 2 * P, v, W, fast_ld);
+        Row r0, r1, r2;
+        unpack(load_raw(rp, v, W, fast_ld), r0);
+        unpack(load_raw(rp + P, v, W, fast_ld), r1);
+        // ALWAYS: the next output row exists, so the prefetch needs no test
+        auto step = [&](const Row& A, const Row& B, Row& C, int u, auto always) {
+            unpack(nx, C);
+            if (decltype(always)::value ? index_ok(u + 3 < H, status)
+                                        : (u + 1 < ue && index_ok(u + 3 < H, status)))
+                nx = load_raw(pf, v, W, fast_ld);
+            pf += P;
+            emit(u, codes_of_row(A, B, C));
+        };
+        const std::true_type yes;
+        const std::false_type no;
+        int u = u0;
+        for (;;) {
+            // rows [u, se) are image rows u+1 .. se of region row ri
+            const int se = HIST ? min(ue, next_b - 1) : ue;
+            for (const int lim = min(se, ue - 1); u + 3 <= lim; u += 3) {
+                step(r0, r1, r2, u, yes);
+                step(r1, r2, r0, u + 1, yes);
+                step(r2, r0, r1, u + 2, yes);
+            }
+            // zero to three rows left in the segment
+            int j = 0;
+            if (u < se) {
+                step(r0, r1, r2, u, no);
+                j = 1;
+                if (u + 1 < se) {
+                    step(r1, r2, r0, u + 1, no);
+                    j = 2;
+                    if (u + 2 < se) {
+                        step(r2, r0, r1, u + 2, no);
+                        j = 3;
+                    }
+                }
+            }
+            u += j;
+            if (u >= ue) break;
+            // region-row boundary: flush the finished region row, move to
+            // the one holding image row u+1, and bring the next two input
+            // rows back to r0, r1
+            if constexpr (HIST) {
+                if (use_smem) flush_slots<MODE, K>(jb, hc, wh, ri, rj_lo, ncs, ncs, status);
+            }
+            while (u + 1 >= next_b) {
+                ++ri;
+                next_b = band_lo(ri + 1, H, hc.R);
+            }
+            if (!use_smem) rowb = ri * hc.C;
+            if (j == 1) {
+                r0 = r1;
+                r1 = r2;
+            } else if (j == 2) {
+                const Row t = r0;
+                r0 = r2;
+                r1 = t;
+            }
+        }
     } else if (v < W - 2 && (!SPLIT || ul < uh)) {  // per-lane global loads, one row ahead
         const uint8_t* rp = jb.img + (size_t)ul * P;
         const uint8_t* pf = rp + 3 * P;  // next input row to prefetch (one row ahead)
@@ -707,39 +824,43 @@ __device__ __forceinline__ void warp_tile(const Job& jb, const HistCfg& hc, int 
 
     if constexpr (HIST) {
         if (use_smem) {
-            __syncwarp();
-            // Only codes that can occur are scanned: the C(8,k) codes with
-            // popcount k for the exact-k LDP modes (bin = position in the
-            // list when compact, the code itself when raw), all 256 for LBP
-            // and the threshold modes.
-            constexpr int NC = exact_k(MODE) ? binom_ce(8, K) : 256;
-            constexpr int NI = (NC + 31) / 32;
-            int code_of[NI];
-#pragma unroll
-            for (int m = 0; m < NI; ++m) {
-                const int idx = lane + 32 * m;
-                // (code 0 of the LDP threshold modes holds the skipped columns)
-                code_of[m] = exact_k(MODE) ? (idx < NC ? (int)__ldg(&g_code_list.code[K][idx]) : -1)
-                                           : ((is_ldp(MODE) && idx == 0) ? -1 : idx);
-            }
-            for (int sl = 0; sl < nslots; ++sl) {
-                const int hbase = ((ri_lo + sl / ncs) * hc.C + rj_lo + sl % ncs) * hc.nbins;
-                uint32_t* hs = wh + sl * 256;
+            if constexpr (kRowSlots) {
+                flush_slots<MODE, K>(jb, hc, wh, ri, rj_lo, ncs, ncs, status);
+            } else {
+                __syncwarp();
+                // Only codes that can occur are scanned: the C(8,k) codes with
+                // popcount k for the exact-k LDP modes (bin = position in the
+                // list when compact, the code itself when raw), all 256 for LBP
+                // and the threshold modes.
+                constexpr int NC = exact_k(MODE) ? binom_ce(8, K) : 256;
+                constexpr int NI = (NC + 31) / 32;
+                int code_of[NI];
 #pragma unroll
                 for (int m = 0; m < NI; ++m) {
-                    const int code = code_of[m];
-                    if (code >= 0) {
-                        const uint32_t c = hs[code];
-                        if (c) {
-                            const int bin = (exact_k(MODE) && hc.compact) ? lane + 32 * m : code;
-                            if (index_ok(hbase + bin < hc.R * hc.C * hc.nbins, status))
-                                atomicAdd(&jb.hist[hbase + bin], c);
-                            hs[code] = 0;
+                    const int idx = lane + 32 * m;
+                    // (code 0 of the LDP threshold modes holds the skipped columns)
+                    code_of[m] = exact_k(MODE) ? (idx < NC ? (int)__ldg(&g_code_list.code[K][idx]) : -1)
+                                               : ((is_ldp(MODE) && idx == 0) ? -1 : idx);
+                }
+                for (int sl = 0; sl < nslots; ++sl) {
+                    const int hbase = ((ri_lo + sl / ncs) * hc.C + rj_lo + sl % ncs) * hc.nbins;
+                    uint32_t* hs = wh + sl * 256;
+#pragma unroll
+                    for (int m = 0; m < NI; ++m) {
+                        const int code = code_of[m];
+                        if (code >= 0) {
+                            const uint32_t c = hs[code];
+                            if (c) {
+                                const int bin = (exact_k(MODE) && hc.compact) ? lane + 32 * m : code;
+                                if (index_ok(hbase + bin < hc.R * hc.C * hc.nbins, status))
+                                    atomicAdd(&jb.hist[hbase + bin], c);
+                                hs[code] = 0;
+                            }
                         }
                     }
                 }
+                __syncwarp();
             }
-            __syncwarp();
         }
     }
 }

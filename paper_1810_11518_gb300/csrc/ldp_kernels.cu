@@ -1,7 +1,8 @@
 // Kernels of libldp for ONE tile variant (rows per warp tile x warps per CTA), compiled
 // once per variant with -DLDP_VAR_ID=<n> -DLDP_VAR_RPW=<rows> -DLDP_VAR_NW=<warps>
 // -DLDP_VAR_MB=<min CTAs per SM> -DLDP_VAR_ST=<1: rows staged through the bulk-copy engine>
-// -DLDP_VAR_SP=<1: narrow tiles split their rows between lane groups>:
+// -DLDP_VAR_SP=<1: narrow tiles split their rows between lane groups, 2: shared
+// histogram slots per region column of the current region row>:
 // the single-image fused kernel and the persistent batch kernel for every
 // (mode, k, histogram) combination, plus their launchers.  Built once more
 // per other reading of Eq. 2-3 with -DLDP_CODE_MODES=<kernel mode> (raw-m
@@ -27,7 +28,8 @@ struct VAR {
     // ST: input rows staged through the bulk-copy ring
     static constexpr int RPW = LDP_VAR_RPW, NW = LDP_VAR_NW, MB = LDP_VAR_MB;
     static constexpr bool ST = LDP_VAR_ST != 0;
-    static constexpr bool SP = LDP_VAR_SP != 0;  // narrow tiles split their rows between lane groups
+    static constexpr bool SP = LDP_VAR_SP == 1;  // narrow tiles split their rows between lane groups
+    static constexpr bool RS = LDP_VAR_SP == 2;  // shared slots per region column of the current region row
 };
 
 
@@ -93,7 +95,7 @@ __global__ void __launch_bounds__(V::NW * 32, V::MB) k_plain(JobArgs ja, HistArg
     WarpRing* ring;
     uint32_t* wh = warp_setup(sh, &ring);
     uint32_t ph = 0;
-    warp_tile<MODE, K, V::RPW, HIST, V::ST, V::SP>(jb, to_hc(ha), (w / ntx) * V::RPW, (w % ntx) * kTileW, wh, ring,
+    warp_tile<MODE, K, V::RPW, HIST, V::ST, V::SP, V::RS>(jb, to_hc(ha), (w / ntx) * V::RPW, (w % ntx) * kTileW, wh, ring,
                                                    ph, ja.status);
 }
 
@@ -136,7 +138,7 @@ __global__ void __launch_bounds__(V::NW * 32, V::MB) k_batch(BatchArgs a) {
         jb.hist = a.hist ? a.hist + hoff : nullptr;
         const int lt = t - (int)wd(10);
         const int ntx = (jb.W - 2 + kTileW - 1) / kTileW;
-        warp_tile<MODE, K, V::RPW, HIST, V::ST, V::SP>(jb, hc, (lt / ntx) * V::RPW, (lt % ntx) * kTileW, wh, ring,
+        warp_tile<MODE, K, V::RPW, HIST, V::ST, V::SP, V::RS>(jb, hc, (lt / ntx) * V::RPW, (lt % ntx) * kTileW, wh, ring,
                                                        ph, a.status);
     }
 }

@@ -58,12 +58,14 @@ struct BatchArgs {
 // split): each warp owns a tile of 128 columns x rows; MB caps registers;
 // staged = 1 feeds the rows through the bulk-copy (TMA) engine into a shared
 // ring; split = 1 lets a tile narrower than 64 columns (an image's last) share
-// its rows between lane groups (for batches of narrow images).
+// its rows between lane groups (for batches of narrow images); split = 2
+// keeps shared histogram slots for the current region row only, flushed at
+// each region-row boundary (small images, whose tiles cross many regions).
 // ldp_kernels.cu is compiled once per entry (the build script reads this list).
 #define LDP_VARIANTS(X)                                                                                      \
     X(0, 64, 4, 5, 0, 0) X(1, 64, 4, 6, 0, 0) X(2, 64, 8, 3, 0, 0) X(3, 64, 4, 4, 1, 0) X(4, 128, 4, 4, 1, 0) \
     X(5, 64, 4, 7, 0, 0) X(6, 64, 8, 4, 0, 0) X(7, 16, 4, 6, 0, 0) X(8, 8, 4, 6, 0, 0) X(9, 64, 4, 7, 0, 1)   \
-    X(10, 128, 4, 7, 0, 0)
+    X(10, 128, 4, 7, 0, 0) X(11, 128, 4, 6, 0, 2) X(12, 128, 4, 7, 0, 2)
 
 #define LDP_DECLARE_VARIANT(ID, RPW, NW, MB, ST, SP)                                                          \
     namespace var##ID {                                                                                   \

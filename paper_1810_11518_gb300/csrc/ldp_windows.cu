@@ -16,8 +16,9 @@
 // stride) and qh rows of cells fit in shared memory, k_window_fused does both
 // in one pass instead: a CTA walks an image's window rows top to bottom in
 // groups, counts each cell row once into a shared-memory ring that holds the
-// cell rows of the current group, and writes the group's window rows
-// straight from the ring -- the cell histograms never reach HBM.
+// cell rows of the current group (one lane per cell, so the reductions of a
+// warp never meet), and writes the group's window rows straight from the
+// ring -- the cell histograms never reach HBM.
 // Images come from ldp_image_desc records (batches) or one record passed by
 // value (single image).
 #include <cuda_runtime.h>
@@ -260,6 +261,7 @@ constexpr int kFusedThreads = 256;
 constexpr int kFusedSmemWords = 40960;    // ring counters at most (160 KB)
 constexpr int kFusedGroupWords = 12288;   // ring size up to which window rows are grouped (48 KB)
 constexpr int kFusedMaxGroup = 8;         // window rows per group at most
+constexpr int kLutCopies = 16;            // copies of the code -> bin table (lane l reads copy l mod 16)
 
 struct FusedArgs {
     const ldp_image_desc* descs;  // nullptr: the single image `one`
@@ -269,7 +271,8 @@ struct FusedArgs {
     int ph;              // row stride in cells
     int wh, ww, sh, sw;  // window size and stride in pixels (window counts)
     int nbins, k;        // as in CellArgs
-    int row_stride;      // ring words per cell row: (cells of the widest image, at least qw) x nbins, rounded to 4
+    int ncp;             // cells per ring row: a multiple of 32 covering the widest image's cells and windows
+    int row_stride;      // ring words per cell row: (nbins + 1) x ncp (bin-major; bin nbins takes codes without one)
     int group;           // window rows per group (G)
     int nslots;          // ring rows: (G - 1) * ph + qh
     int rows_per_band;   // window rows per work item
@@ -283,32 +286,35 @@ struct FusedArgs {
 // G window rows.  Per group: the cell rows the group covers that are not yet
 // in the ring are zeroed and counted (ring slot = cell row mod nslots; the
 // nslots = (G-1) ph + qh rows of a group are distinct mod nslots, rows past
-// the image stay out), then every output word e = b*nbins + bin of each of
-// the G window rows is the sum over the window row's cell rows of the ring
-// words e + c*nbins, c < qw (window b covers cells b .. b+qw-1 of the row;
-// cells past the image are zero).  Three barriers per group.  The group's
-// (128-column block, image row) tasks are split into equal runs of
-// consecutive tasks, one per warp (a lane takes four consecutive columns,
-// their cells found once per block), four rows' loads in flight; small CTAs
-// (eight warps, four per SM) keep the barriers' idle time short.
-// Counts are shared-memory reductions without a branch (a column past the
-// image or a code without a bin counts into a junk word past the ring).
+// the image stay out), then each output word (window b, bin) of the G window
+// rows is the sum over the window's qh x qw cells of their ring words.
+// Three barriers per group.
+// Ring rows are bin-major: the counter of (cell c, bin) is word bin * ncp + c,
+// ncp a multiple of 32.  Counting gives each lane one cell: units (image row,
+// block of 32 cells) are split evenly over the warps, and lane l counts the
+// row's pixels of cell 32 * block + l, so the 32 reductions of one
+// instruction hit 32 different counters in 32 different banks, whatever the
+// codes.  The code -> bin table (16-bit entries) is replicated 16 times,
+// lane l reading copy l mod 16: two lanes can only meet in a bank when
+// (l mod 16) / 2 agree, at most four lanes.  Output items (four bins, a
+// block of 32 windows) go to the warps in turn, a lane per window: a warp
+// reads 32 consecutive cells of a bin row per load.
 __global__ void __launch_bounds__(kFusedThreads, 4) k_window_fused(FusedArgs a, int count) {
-    extern __shared__ uint4 ring4[];  // nslots x row_stride counters, then 4 junk words
+    extern __shared__ uint4 ring4[];  // nslots x row_stride counters
     uint32_t* ring = reinterpret_cast<uint32_t*>(ring4);
-    __shared__ int lut4[256];  // 4 x the bin of each code, -1 for codes without a bin
-    for (int c = threadIdx.x; c < 256; c += blockDim.x) {
+    __shared__ uint16_t lut[256 * kLutCopies];  // bin of each code (nbins for codes without one), per copy
+    for (int e = threadIdx.x; e < 256 * kLutCopies; e += blockDim.x) {
+        const int c = e / kLutCopies;
         const int b = (a.k >= 1) ? (int)__ldg(&g_bin_table.bin[a.k][c]) : c;
-        lut4[c] = b >= 0 ? 4 * b : -1;
+        lut[e] = (uint16_t)(b >= 0 ? b : a.nbins);
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    const float inv_cw = 1.0f / (float)a.cw, inv_ch = 1.0f / (float)a.ch;
-    const int rs = a.row_stride, ns = a.nslots;
+    const int rs = a.row_stride, ns = a.nslots, ncp = a.ncp;
     const uint32_t ring_addr = (uint32_t)__cvta_generic_to_shared(ring);
-    // one word past the ring takes the counts of columns past the image and of
-    // codes without a bin, so the count needs no branch
-    const uint32_t junk_addr = (uint32_t)__cvta_generic_to_shared(ring + ns * rs);
-    const uint32_t ring_bytes = 4u * (uint32_t)(ns * rs + 4);  // ring and junk words (checked builds)
+    const uint32_t ring_bytes = 4u * (uint32_t)(ns * rs);  // (checked builds)
+    // this lane's copy of the table: byte address of entry 0
+    const uint32_t lut_lane = (uint32_t)__cvta_generic_to_shared(lut) + 2u * (uint32_t)(lane & (kLutCopies - 1));
+    const uint32_t bin_bytes = 4u * (uint32_t)ncp;  // bytes between the bin rows of a ring row
     const uint64_t items = (uint64_t)count * (uint64_t)a.bands;
     for (uint64_t it = blockIdx.x; it < items; it += gridDim.x) {
         const int img = (int)(it / (uint64_t)a.bands), band = (int)(it % (uint64_t)a.bands);
@@ -319,85 +325,89 @@ __global__ void __launch_bounds__(kFusedThreads, 4) k_window_fused(FusedArgs a, 
         const int a0 = band * a.rows_per_band, a1 = min(a0 + a.rows_per_band, nwr);
         if (a0 >= a1) continue;
         const int ncr = (H + a.ch - 1) / a.ch;
+        const int ncc = (W - 2) / a.cw + 1;  // cells holding interior columns
+        const int nblk = (ncc + 31) / 32;
         const int words = nwc * a.nbins;
         uint32_t* out_img = a.hist + d.hist_offset;
         const bool vec = (a.nbins & 3) == 0 && ((reinterpret_cast<uintptr_t>(out_img) & 15u) == 0);
-        const bool al = ((reinterpret_cast<uintptr_t>(d.codes) | (uintptr_t)d.code_pitch) & 3u) == 0;
-        const int ncb = (W - 2 + 127) / 128;
 
-        // the lane's four columns of block cb: byte offsets of their cells
-        // within a ring row (4 * cell * nbins) and which lie inside
-        auto block_cells = [&](int cb, uint32_t(&off4)[4], bool(&in)[4]) {
-            const int yq = 1 + cb * 128 + 4 * lane;  // columns yq .. yq+3
-#pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                in[t] = yq + t < W - 1;
-                off4[t] = in[t] ? 4u * (uint32_t)(cell_of(yq + t, a.cw, inv_cw) * a.nbins) : 0u;
-            }
-        };
-        // image rows x0, x0 + step, ... < x1 of column block cb, each into the
-        // ring row of its cell row (cell rows n0 .. n0 + nslots - 1; n0 in
-        // ring row s_n0), four rows' loads in flight.  A row whose 128 codes
-        // all have a bin and lie inside counts without a test per pixel.
-        auto count_rows = [&](int cb, const uint32_t(&off4)[4], const bool(&in)[4], int x0, int x1, int step,
-                              int n0, int s_n0) {
-            const int yq = 1 + cb * 128 + 4 * lane;
-            const bool v4 = al && in[3];
-            const size_t pstep = (size_t)step * (size_t)d.code_pitch;
-            const uint8_t* p = d.codes + (size_t)(x0 - 1) * (size_t)d.code_pitch + (yq - 1);
-            int cr = cell_of(x0, a.ch, inv_ch);  // cell row of the current image row, ending before nb
-            int sl = s_n0 + (cr - n0);
-            if (sl >= ns) sl -= ns;
-            uint32_t sbase = ring_addr + 4u * (uint32_t)(sl * rs);
-            int nb = (cr + 1) * a.ch;
-            for (int x = x0; x < x1; x += 4 * step, p += 4 * pstep) {
-                uint32_t w[4];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const uint8_t* cp = p + j * pstep;
-                    w[j] = 0;
-                    if (x + j * step < x1) {
-                        if (v4) {
-                            w[j] = __ldg(reinterpret_cast<const unsigned int*>(cp));
-                        } else {
-#pragma unroll
-                            for (int t = 0; t < 4; ++t)
-                                if (in[t]) w[j] |= (uint32_t)__ldg(cp + t) << (8 * t);
-                        }
-                    }
+        const bool al = ((reinterpret_cast<uintptr_t>(d.codes) | (uintptr_t)d.code_pitch) & 3u) == 0;
+        // count image rows [xa, xb) of cell block cb: lane l takes cell
+        // 32 cb + l (code columns s0 .. s0+n-1 of each row), each code one
+        // reduction into the ring row of its cell row
+        auto count_rows = [&](int cb, int xa, int xb, auto cw_c) {
+            constexpr int CW = decltype(cw_c)::value;  // a.cw when it is at most 13, else 0
+            const int c = cb * 32 + lane;
+            const int s0 = max(c * a.cw - 1, 0), e0 = min(c * a.cw + a.cw - 1, W - 2);
+            const int n = c < ncc ? max(e0 - s0, 0) : 0;
+            int r = xa / a.ch;  // cell row of image row xa
+            int s = r % ns, nb = (r + 1) * a.ch;
+            uint32_t rb = ring_addr + 4u * (uint32_t)(s * rs + c);
+            // one code: its bin from this lane's copy of the table, one
+            // reduction (a position past the cell's columns counts into the
+            // cell's word of the spare bin row: no branch)
+            auto one = [&](uint32_t code, bool ok) {
+                const uint32_t bin = ok ? (uint32_t)lut[code * kLutCopies + (lane & (kLutCopies - 1))]
+                                        : (uint32_t)a.nbins;
+                uint32_t addr;
+                asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(addr) : "r"(bin), "r"(bin_bytes), "r"(rb));
+                if (index_ok(addr - ring_addr < ring_bytes, a.status))
+                    asm volatile("red.shared.add.u32 [%0], 1;" ::"r"(addr));
+            };
+            auto next_row = [&](int x) {
+                if (x >= nb) {  // into the next cell row
+                    nb += a.ch;
+                    if (++s == ns) s = 0;
+                    rb = ring_addr + 4u * (uint32_t)(s * rs + c);
                 }
+            };
+            if constexpr (CW > 0) {
+                // the cell's bytes come from four aligned words at s0 & ~3 (one
+                // row ahead) when they lie inside the row, else byte by byte
+                const int base = s0 & ~3;
+                const uint32_t sh = 8u * (uint32_t)(s0 & 3);
+                const bool words = al && base + 16 <= W - 2;
+                const uint8_t* rp = d.codes + (size_t)(xa - 1) * (size_t)d.code_pitch;
+                auto fetch = [&](const uint8_t* row, uint32_t(&w)[4]) {
+                    if (words) {
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int xx = x + j * step;
-                    if (xx < x1) {
-                        while (xx >= nb) {  // into the next cell row
-                            nb += a.ch;
-                            if (++sl == ns) sl = 0;
-                            sbase = ring_addr + 4u * (uint32_t)(sl * rs);
-                        }
-                        int b4[4];
+                        for (int i = 0; i < 4; ++i) w[i] = __ldg(reinterpret_cast<const unsigned int*>(row + base) + i);
+                    } else {  // the bytes of the cell's columns only
 #pragma unroll
-                        for (int t = 0; t < 4; ++t) b4[t] = lut4[(w[j] >> (8 * t)) & 0xFFu];
-                        const bool ok = in[3] && (b4[0] | b4[1] | b4[2] | b4[3]) >= 0;
-                        if (__all_sync(0xffffffffu, ok)) {
-#pragma unroll
-                            for (int t = 0; t < 4; ++t) {
-                                const uint32_t addr = sbase + off4[t] + (uint32_t)b4[t];
-                                if (index_ok(addr - ring_addr < ring_bytes, a.status))
-                                    asm volatile("red.shared.add.u32 [%0], 1;" ::"r"(addr) : "memory");
-                            }
-                        } else {
+                        for (int i = 0; i < 4; ++i) {
+                            w[i] = 0;
 #pragma unroll
                             for (int t = 0; t < 4; ++t) {
-                                const uint32_t addr =
-                                    (in[t] && b4[t] >= 0) ? sbase + off4[t] + (uint32_t)b4[t] : junk_addr;
-                                if (index_ok(addr - ring_addr < ring_bytes, a.status))
-                                    asm volatile("red.shared.add.u32 [%0], 1;" ::"r"(addr) : "memory");
+                                const int col = base + 4 * i + t;
+                                if (col >= s0 && col < s0 + n) w[i] |= (uint32_t)__ldg(row + col) << (8 * t);
                             }
                         }
                     }
+                };
+                uint32_t w[4], nx[4];
+                if (xa < xb) fetch(rp, nx);
+                for (int x = xa; x < xb; ++x) {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) w[i] = nx[i];
+                    rp += d.code_pitch;
+                    if (x + 1 < xb) fetch(rp, nx);
+                    next_row(x);
+                    // bytes j = 0 .. CW-1 of the cell at positions 4i .. 4i+3 of av[i]
+                    constexpr int NA = (CW + 3) / 4;
+                    uint32_t av[NA];
+#pragma unroll
+                    for (int i = 0; i < NA; ++i) av[i] = __funnelshift_r(w[i], i + 1 < 4 ? w[i + 1] : 0u, sh);
+#pragma unroll
+                    for (int j = 0; j < CW; ++j) one(prmt(av[j >> 2], 0u, 0x4440u | (uint32_t)(j & 3)), j < n);
+                }
+            } else {
+                const uint8_t* rp = d.codes + (size_t)(xa - 1) * (size_t)d.code_pitch + s0;
+                for (int x = xa; x < xb; ++x, rp += d.code_pitch) {
+                    next_row(x);
+                    for (int j = 0; j < n; ++j) one(__ldg(rp + j), true);
                 }
             }
+            asm volatile("" ::: "memory");  // the reductions come before the barrier that follows
         };
 
         int next = a0 * a.ph;  // first cell row not in the ring
@@ -412,21 +422,18 @@ __global__ void __launch_bounds__(kFusedThreads, 4) k_window_fused(FusedArgs a, 
             }
             __syncthreads();
             if (n0 < n1) {
-                // image rows of cell rows [n0, n1) that hold codes; tasks
-                // (column block, row) in block-major order, an equal share of
-                // consecutive tasks per warp (one or two blocks each)
+                // units (cell block, image row) of cell rows [n0, n1), block-major,
+                // an equal share of consecutive units per warp
                 const int x0 = max(n0 * a.ch, 1), x1 = min(n1 * a.ch, H - 1);
-                const int s_n0 = n0 % ns;
                 const int R = x1 - x0;
                 if (R > 0) {
-                    const int T = R * ncb;
+                    const int T = R * nblk;
                     const int t1 = (int)((int64_t)T * (warp + 1) / nwarps);
                     for (int t = (int)((int64_t)T * warp / nwarps); t < t1;) {
                         const int cb = t / R, r0 = t - cb * R, r1 = min(R, r0 + (t1 - t));
-                        uint32_t off[4];
-                        bool in[4];
-                        block_cells(cb, off, in);
-                        count_rows(cb, off, in, x0 + r0, x0 + r1, 1, n0, s_n0);
+                        if (a.cw == 10) count_rows(cb, x0 + r0, x0 + r1, std::integral_constant<int, 10>{});
+                        else if (a.cw <= 13) count_rows(cb, x0 + r0, x0 + r1, std::integral_constant<int, 13>{});
+                        else count_rows(cb, x0 + r0, x0 + r1, std::integral_constant<int, 0>{});
                         t += r1 - r0;
                     }
                 }
@@ -436,47 +443,60 @@ __global__ void __launch_bounds__(kFusedThreads, 4) k_window_fused(FusedArgs a, 
             for (int wa = g0; wa < g1; ++wa) {
                 const int r0 = wa * a.ph, nr = min(a.qh, ncr - r0), s0 = r0 % ns;
                 uint32_t* out = out_img + (uint64_t)wa * (uint64_t)words;
+                // items (bin group q, block of 32 windows): lane l takes window
+                // 32 * block + l, so a warp's loads read 32 consecutive cells of
+                // one bin row (32 banks); the warps take items in turn
+                const int nq = vec ? a.nbins / 4 : a.nbins;
+                const int nbw = (nwc + 31) / 32;
                 // QW: qw when it is a small constant (unrolled), else 0 (a loop)
-                auto emit_vec = [&](auto qw_c) {
+                auto emit = [&](auto qw_c) {
                     constexpr int QW = decltype(qw_c)::value;
-                    for (int e = 4 * threadIdx.x; e < words; e += 4 * blockDim.x) {
-                        uint4 acc = make_uint4(0, 0, 0, 0);
-                        int sidx = s0;
-                        for (int ri = 0; ri < nr; ++ri) {
-#pragma unroll
-                            for (int c = 0; c < (QW ? QW : a.qw); ++c) {
-                                const int ix = sidx * rs + e + c * a.nbins;
-                                if (!index_ok(ix + 3 < ns * rs, a.status)) continue;
-                                const uint4 v = *reinterpret_cast<const uint4*>(ring + ix);
-                                acc.x += v.x;
-                                acc.y += v.y;
-                                acc.z += v.z;
-                                acc.w += v.w;
-                            }
-                            if (++sidx == ns) sidx = 0;
+                    // item = (q, block bb) = q * nbw + bb, stepped by the warp count
+                    const int dbb = nwarps % nbw, dq = nwarps / nbw;
+                    for (int q = warp / nbw, bb = warp % nbw; q < nq;) {
+                        const int b = bb * 32 + lane;
+                        bb += dbb;
+                        const int qi = q;
+                        q += dq;
+                        if (bb >= nbw) {
+                            bb -= nbw;
+                            ++q;
                         }
-                        __stcs(reinterpret_cast<uint4*>(out + e), acc);
+                        if (b >= nwc) continue;
+                        if (vec) {
+                            uint4 acc = make_uint4(0, 0, 0, 0);
+                            int sidx = s0;
+                            for (int ri = 0; ri < nr; ++ri) {
+                                const uint32_t* rw = ring + sidx * rs + 4 * qi * ncp + b;
+#pragma unroll
+                                for (int c = 0; c < (QW ? QW : a.qw); ++c) {
+                                    if (!index_ok(sidx * rs + (4 * qi + 3) * ncp + b + c < ns * rs, a.status)) continue;
+                                    acc.x += rw[c];
+                                    acc.y += rw[c + ncp];
+                                    acc.z += rw[c + 2 * ncp];
+                                    acc.w += rw[c + 3 * ncp];
+                                }
+                                if (++sidx == ns) sidx = 0;
+                            }
+                            __stcs(reinterpret_cast<uint4*>(out + (size_t)b * a.nbins + 4 * qi), acc);
+                        } else {
+                            uint32_t acc = 0;
+                            int sidx = s0;
+                            for (int ri = 0; ri < nr; ++ri) {
+                                const uint32_t* rw = ring + sidx * rs + qi * ncp + b;
+                                for (int c = 0; c < (QW ? QW : a.qw); ++c)
+                                    if (index_ok(sidx * rs + qi * ncp + b + c < ns * rs, a.status)) acc += rw[c];
+                                if (++sidx == ns) sidx = 0;
+                            }
+                            out[(size_t)b * a.nbins + qi] = acc;
+                        }
                     }
                 };
-                if (vec) {
-                    if (a.qw == 1) emit_vec(std::integral_constant<int, 1>{});
-                    else if (a.qw == 2) emit_vec(std::integral_constant<int, 2>{});
-                    else if (a.qw == 3) emit_vec(std::integral_constant<int, 3>{});
-                    else if (a.qw == 4) emit_vec(std::integral_constant<int, 4>{});
-                    else emit_vec(std::integral_constant<int, 0>{});
-                } else {
-                    for (int e = threadIdx.x; e < words; e += blockDim.x) {
-                        uint32_t acc = 0;
-                        int sidx = s0;
-                        for (int ri = 0; ri < nr; ++ri) {
-                            const uint32_t* sl = ring + sidx * rs + e;
-                            for (int c = 0; c < a.qw; ++c)
-                                if (index_ok(sidx * rs + e + c * a.nbins < ns * rs, a.status)) acc += sl[c * a.nbins];
-                            if (++sidx == ns) sidx = 0;
-                        }
-                        out[e] = acc;
-                    }
-                }
+                if (a.qw == 1) emit(std::integral_constant<int, 1>{});
+                else if (a.qw == 2) emit(std::integral_constant<int, 2>{});
+                else if (a.qw == 3) emit(std::integral_constant<int, 3>{});
+                else if (a.qw == 4) emit(std::integral_constant<int, 4>{});
+                else emit(std::integral_constant<int, 0>{});
             }
         }
     }
@@ -505,17 +525,21 @@ namespace {
 // grouped.
 struct FusedPlan {
     uint64_t rs = 0;
-    int group = 1, nslots = 1;
+    int ncp = 0, group = 1, nslots = 1;
 };
 
 FusedPlan fused_plan(int max_W, const WindowGeom& g) {
     FusedPlan p;
     if (window_direct(g) || g.ww % g.sw != 0) return p;
     const int ch = gcd_int(g.wh, g.sh), qh = g.wh / ch, qw = g.ww / g.sw, ph = g.sh / ch;
-    const int ncc = (max_W + g.sw - 1) / g.sw;
-    const uint64_t rs = ((uint64_t)(ncc > qw ? ncc : qw) * (uint64_t)g.nbins + 3u) & ~(uint64_t)3u;
+    // cells a window row reads: the last window starts in cell (max_W - 1) / sw
+    // at most and spans qw cells; counted cells end before that
+    const int ncells = (max_W - 1) / g.sw + qw;
+    const int ncp = (ncells + 31) / 32 * 32;
+    const uint64_t rs = (uint64_t)(g.nbins + 1) * (uint64_t)ncp;
     if ((uint64_t)qh * rs > (uint64_t)kFusedSmemWords) return p;
     p.rs = rs;
+    p.ncp = ncp;
     p.nslots = qh;
     if (ph <= qh)
         for (int G = 2; G <= kFusedMaxGroup; ++G) {
@@ -546,7 +570,7 @@ cudaError_t launch_windows(const ldp_image_desc* d_descs, const ldp_image_desc* 
     if (!status) return cudaErrorInvalidSymbol;
     if (const FusedPlan fp = fused_plan(max_W, g); fp.rs) {
         cudaError_t e = cudaFuncSetAttribute(k_window_fused, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)((kFusedSmemWords + 4) * sizeof(uint32_t)));
+                                             (int)(kFusedSmemWords * sizeof(uint32_t)));
         if (e != cudaSuccess) return e;
         FusedArgs fa{};
         fa.descs = d_descs;
@@ -563,13 +587,14 @@ cudaError_t launch_windows(const ldp_image_desc* d_descs, const ldp_image_desc* 
         fa.nbins = g.nbins;
         fa.k = g.compact ? g.k : 0;
         fa.row_stride = (int)fp.rs;
+        fa.ncp = fp.ncp;
         fa.group = fp.group;
         fa.nslots = fp.nslots;
         fa.hist = hist;
         fa.max_H = max_H;
         fa.max_W = max_W;
         fa.status = status;
-        const size_t smem = sizeof(uint32_t) * ((size_t)fp.rs * (size_t)fp.nslots + 4);
+        const size_t smem = sizeof(uint32_t) * (size_t)fp.rs * (size_t)fp.nslots;
         int occ = 0;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_window_fused, kFusedThreads, smem);
         if (e != cudaSuccess) return e;

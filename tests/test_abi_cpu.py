@@ -43,7 +43,7 @@ def test_variants_listed(lib):
     assert nv == len(libbuild.variants()) and nv >= 1
     for v in range(nv):
         name = lib.ldp_variant_name(v).decode()
-        assert re.fullmatch(r"r\d+w\d+b\d+t[01]s?", name)
+        assert re.fullmatch(r"r\d+w\d+b\d+t[01][sf]?", name)
     assert lib.ldp_variant_name(nv) == b""
     assert lib.ldp_set_plain_variant(nv) == 1
     assert lib.ldp_set_plain_variant(-2) == 1
@@ -233,7 +233,7 @@ def test_autotune_cache_names_compiled_variants():
     from paper_1810_11518_gb300 import autotune
     from paper_1810_11518_gb300 import build as libbuild
 
-    names = [f"r{rpw}w{nw}b{mb}t{st}" + ("s" if sp else "") for _, rpw, nw, mb, st, sp in libbuild.variants()]
+    names = [f"r{rpw}w{nw}b{mb}t{st}" + {0: "", 1: "s", 2: "f"}[sp] for _, rpw, nw, mb, st, sp in libbuild.variants()]
     with open(autotune.DEFAULT_CACHE) as f:
         cache = json.load(f)
     assert cache
