@@ -23,6 +23,7 @@
 // value (single image).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <type_traits>
 
@@ -532,9 +533,11 @@ FusedPlan fused_plan(int max_W, const WindowGeom& g) {
     FusedPlan p;
     if (window_direct(g) || g.ww % g.sw != 0) return p;
     const int ch = gcd_int(g.wh, g.sh), qh = g.wh / ch, qw = g.ww / g.sw, ph = g.sh / ch;
-    // cells a window row reads: the last window starts in cell (max_W - 1) / sw
-    // at most and spans qw cells; counted cells end before that
-    const int ncells = (max_W - 1) / g.sw + qw;
+    // cells of a ring row: those a window row reads (the last window of the
+    // widest image starts in cell nwc - 1 and spans qw cells) and those
+    // holding interior columns
+    const int nwc = max_W <= g.ww ? 1 : (max_W - g.ww + g.sw - 1) / g.sw + 1;
+    const int ncells = std::max(nwc + qw - 1, (max_W - 2) / g.sw + 1);
     const int ncp = (ncells + 31) / 32 * 32;
     const uint64_t rs = (uint64_t)(g.nbins + 1) * (uint64_t)ncp;
     if ((uint64_t)qh * rs > (uint64_t)kFusedSmemWords) return p;
