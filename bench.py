@@ -79,9 +79,9 @@ def dist_env():
 # profiles/k_batch_ldp_k3_512img_full.md), scaled to a launch by its pixels.
 # Valid only for the kernel sources it was taken on: any change to them
 # reports traffic as null until a new capture is recorded here.
-TRAFFIC_PER_PX = 303.933e6 / (512 * 640 * 490)
+TRAFFIC_PER_PX = (176.721920e6 + 126.171392e6) / (512 * 640 * 490)
 TRAFFIC_SOURCES = ("paper_1810_11518_gb300/csrc/ldp_device.cuh", "paper_1810_11518_gb300/csrc/ldp_kernels.cu")
-TRAFFIC_SHA256 = "0f4de6b006a1fd41dbca14e4671a5f81e7755c1ceee4520fc186060f20f5114d"
+TRAFFIC_SHA256 = "f4e83fb588d44b3b235e692a0fc01c57385c10d6a28720ab4f328b7353bef1d7"
 
 
 # Warp-instruction issue slots x 32 per input pixel of the same kernel, from
