@@ -377,9 +377,11 @@ typedef struct {
     uint64_t completed, pixels, batches, pending, arena_used, arena_bytes;
 } ldp_server_stats_t;
 
-/* Creates the runtime (allocates the arena and per-stream buffers, starts a
+/* Creates the runtime (allocates the arena and per-stream buffers, runs each
+ * stream's batch plans once on an empty batch so that their kernels are
+ * loaded and their CUDA graphs captured before the first request, starts a
  * dispatcher and a completion thread).  EINVAL on a bad config, ENOMEM when
- * an allocation fails. */
+ * an allocation fails, ECUDA when the warm-up fails. */
 LDP_API int ldp_server_create(ldp_server **out, const ldp_server_config *cfg);
 
 /* Queues one request.  host_img (H x W, row pitch `pitch`) must stay valid

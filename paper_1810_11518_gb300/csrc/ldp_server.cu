@@ -392,6 +392,24 @@ int ldp_server_create(ldp_server** out, const ldp_server_config* cfg) {
         cudaGetLastError();
         return ldp::report_error(LDP_ENOMEM, "server buffer allocation failed");
     }
+    // warm every plan up with an empty batch: its kernels' modules load and
+    // its CUDA graph is captured now, not inside the first request that
+    // happens to need it (that costs milliseconds)
+    for (Slot& sl : s->slots) {
+        e = cudaMemsetAsync(sl.d_count, 0, sizeof(int), sl.stream);
+        for (ldp_batch_plan* pl : {sl.plan, sl.plan_short})
+            if (e == cudaSuccess && pl &&
+                ldp_batch_run(pl, sl.d_desc, sl.d_count, s->hist_len ? sl.d_hist : nullptr, sl.stream) != LDP_OK)
+                e = cudaErrorUnknown;
+        if (e == cudaSuccess) e = cudaStreamSynchronize(sl.stream);
+        if (e != cudaSuccess) {
+            const std::string why = std::string("server warm-up: ") + ldp_last_error();
+            destroy_resources(s);
+            delete s;
+            cudaGetLastError();
+            return ldp::report_error(LDP_ECUDA, why.c_str());
+        }
+    }
     s->dispatcher = std::thread(dispatcher_main, s);
     s->completer = std::thread(completer_main, s);
     *out = s;
