@@ -307,7 +307,9 @@ LDP_API int ldp_num_variants(void);
 LDP_API const char *ldp_variant_name(int variant);
 /* Variant used by the single-image entry points; -1 (the default) chooses
  * by image size: short warp tiles for images of few 64-row tiles (their
- * latency is that of one tile), 64-row tiles for large images. */
+ * latency is that of one tile: 4-row tiles while the image has fewer 8-row
+ * tiles than the GPU has warp schedulers, then 8 and 16 rows), 64-row
+ * tiles for large images. */
 LDP_API int ldp_set_plain_variant(int variant);
 
 /* ---- host-to-host pipeline: copies and compute overlapped ---- */

@@ -27,11 +27,12 @@ int check_regions(int R, int C) {
 
 // Tile variant of a single-image launch: an image of few 64-row tiles keeps
 // most SMs idle and its latency is that of one tile, so smaller images take
-// shorter warp tiles (more tiles in flight); large images keep 64-row tiles
-// (less flush overhead per pixel).  The first non-staged variant of each
-// height is used.
+// shorter warp tiles (more tiles in flight; 4-row tiles while the image has
+// fewer 8-row tiles than the GPU has warp schedulers); large images keep
+// 64-row tiles (less flush overhead per pixel).  The first non-staged
+// variant of each height is used.
 struct PlainChoice {
-    int v8 = 0, v16 = 0, sms = 132;
+    int v4 = -1, v8 = 0, v16 = 0, sms = 132;
 };
 
 // the short-tile variants and the SM count, found once (thread-safe static)
@@ -43,6 +44,7 @@ const PlainChoice& plain_choice() {
             const char* name = ldp::variant_name(v);
             const int th = ldp::variant_tile_h(v);
             const bool staged = name[0] && name[strlen(name) - 1] == '1';
+            if (!staged && th == 4 && r.v4 < 0) r.v4 = v;
             if (!staged && th == 8 && !f8) r.v8 = v, f8 = true;
             if (!staged && th == 16 && !f16) r.v16 = v, f16 = true;
         }
@@ -60,6 +62,8 @@ int plain_variant(int H, int W) {
     if (fixed >= 0) return fixed;
     const PlainChoice& c = plain_choice();
     const long long tiles64 = (long long)((H - 2 + 63) / 64) * (long long)((W - 2 + 127) / 128);
+    const long long tiles8 = (long long)((H - 2 + 7) / 8) * (long long)((W - 2 + 127) / 128);
+    if (c.v4 >= 0 && tiles8 < 4LL * c.sms) return c.v4;  // fewer 8-row tiles than warp schedulers
     if (tiles64 < 2LL * c.sms) return c.v8;
     if (tiles64 < 8LL * c.sms) return c.v16;
     return 0;

@@ -65,7 +65,7 @@ struct BatchArgs {
 #define LDP_VARIANTS(X)                                                                                      \
     X(0, 64, 4, 5, 0, 0) X(1, 64, 4, 6, 0, 0) X(2, 64, 8, 3, 0, 0) X(3, 64, 4, 4, 1, 0) X(4, 128, 4, 4, 1, 0) \
     X(5, 64, 4, 7, 0, 0) X(6, 64, 8, 4, 0, 0) X(7, 16, 4, 6, 0, 0) X(8, 8, 4, 6, 0, 0) X(9, 64, 4, 7, 0, 1)   \
-    X(10, 128, 4, 7, 0, 0) X(11, 128, 4, 6, 0, 2) X(12, 128, 4, 7, 0, 2)
+    X(10, 128, 4, 7, 0, 0) X(11, 128, 4, 6, 0, 2) X(12, 128, 4, 7, 0, 2) X(13, 4, 4, 6, 0, 0)
 
 #define LDP_DECLARE_VARIANT(ID, RPW, NW, MB, ST, SP)                                                          \
     namespace var##ID {                                                                                   \

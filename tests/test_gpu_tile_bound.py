@@ -85,7 +85,7 @@ def test_set_config_grows_the_work_list_of_a_used_plan(env):
 def test_autotune_drops_truncated_variants(env):
     """A plan created with max_pixels below the batch's real pixel count (the
     caller broke its own bound): variants of 64 rows and more still fit the
-    work list, the 8- and 16-row ones do not and are clamped on the device.
+    work list, the 4-, 8- and 16-row ones do not and are clamped on the device.
     Those would time fastest (less work); the tuner must flag and skip them."""
     torch, ldp, oracle, synth = env
     from paper_1810_11518_gb300 import autotune
@@ -96,7 +96,7 @@ def test_autotune_drops_truncated_variants(env):
         res = autotune.tune_plan(plan, d_desc, d_count, d_hist, ctas_options=(0,), reps=2, warmup=1)
         flagged = {r["name"] for r in res["all"] if r["status"]}
         short = {ldp.variant_name(v) for v in range(ldp.num_variants())
-                 if ldp.variant_name(v).startswith(("r8w", "r16w"))}
+                 if ldp.variant_name(v).startswith(("r4w", "r8w", "r16w"))}
         assert short and flagged == short
         assert all(r["status"] & 2 for r in res["all"] if r["status"])
         assert res["name"] not in flagged
