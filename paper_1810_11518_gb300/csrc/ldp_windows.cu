@@ -259,10 +259,17 @@ __global__ void __launch_bounds__(256) k_window_sum(SumArgs a, int count, int nw
 }
 
 constexpr int kFusedThreads = 256;
-constexpr int kFusedSmemWords = 40960;    // ring counters at most (160 KB)
-constexpr int kFusedGroupWords = 12288;   // ring size up to which window rows are grouped (48 KB)
+constexpr int kFusedWarps = kFusedThreads / 32;
+constexpr int kFusedSmemWords = 40960;    // ring + staging at most (160 KB)
+constexpr int kFusedGroupWords = 14080;   // ring + staging up to which window rows are grouped (55 KB: 4 CTAs per SM)
 constexpr int kFusedMaxGroup = 8;         // window rows per group at most
-constexpr int kLutCopies = 16;            // copies of the code -> bin table (lane l reads copy l mod 16)
+
+// 32-bit load from shared memory at byte address a.
+__device__ __forceinline__ uint32_t lds32(uint32_t a) {
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a));
+    return v;
+}
 
 struct FusedArgs {
     const ldp_image_desc* descs;  // nullptr: the single image `one`
@@ -271,9 +278,10 @@ struct FusedArgs {
     int qh, qw;          // window size in cells
     int ph;              // row stride in cells
     int wh, ww, sh, sw;  // window size and stride in pixels (window counts)
-    int nbins, k;        // as in CellArgs
+    int nbins, k;        // as in CellArgs (nbins even)
     int ncp;             // cells per ring row: a multiple of 32 covering the widest image's cells and windows
-    int row_stride;      // ring words per cell row: (nbins + 1) x ncp (bin-major; bin nbins takes codes without one)
+    int row_stride;      // ring words per cell row: (nbins / 2 + 1) x ncp (bin pairs, pair nbins / 2 takes codes without a bin)
+    int stage_words;     // staging words per window row: the widest image's windows x nbins
     int group;           // window rows per group (G)
     int nslots;          // ring rows: (G - 1) * ph + qh
     int rows_per_band;   // window rows per work item
@@ -288,37 +296,47 @@ struct FusedArgs {
 // in the ring are zeroed and counted (ring slot = cell row mod nslots; the
 // nslots = (G-1) ph + qh rows of a group are distinct mod nslots, rows past
 // the image stay out), then each output word (window b, bin) of the G window
-// rows is the sum over the window's qh x qw cells of their ring words.
-// Three barriers per group.
-// Ring rows are bin-major: the counter of (cell c, bin) is word bin * ncp + c,
-// ncp a multiple of 32.  Counting gives each lane one cell: units (image row,
-// block of 32 cells) are split evenly over the warps, and lane l counts the
-// row's pixels of cell 32 * block + l, so the 32 reductions of one
-// instruction hit 32 different counters in 32 different banks, whatever the
-// codes.  The code -> bin table (16-bit entries) is replicated 16 times,
-// lane l reading copy l mod 16: two lanes can only meet in a bank when
-// (l mod 16) / 2 agree, at most four lanes.  Output items (four bins, a
-// block of 32 windows) go to the warps in turn, a lane per window: a warp
-// reads 32 consecutive cells of a bin row per load.
+// rows is the sum over the window's qh x qw cells of their ring counters,
+// written to a shared staging copy of the G window rows, which leaves for
+// HBM as one contiguous block (16-byte stores of consecutive addresses)
+// while the next group is zeroed.  Three barriers per group.
+// Counters are 16 bits, two bins to a word: bin j of cell c is half j & 1 of
+// word (j >> 1) * ncp + c of its ring row (ncp a multiple of 32), so a cell
+// of at most 65535 pixels cannot carry into the other half, and sums of such
+// words over a window of at most 65535 pixels stay exact in each half.
+// Counting gives each lane one cell: units (image row, block of 32 cells) are
+// split evenly over the warps, and lane l counts the row's pixels of cell
+// 32 * block + l, so the 32 reductions of one instruction hit 32 different
+// words in 32 different banks, whatever the codes.  The code table holds,
+// per code, the byte offset of its bin pair's word row plus 16 for the upper
+// half: the reduction adds 1 << (entry mod 32) at the offset rounded down to
+// 32.  Output items (a block of 32 windows and four bins -- two pair rows --
+// or, when nbins is not a multiple of four, two bins) go to the warps in
+// turn, a lane per window: a warp reads 32 consecutive cells of a pair row per
+// load, and each cell row of a pair of window rows once.
+
 __global__ void __launch_bounds__(kFusedThreads, 4) k_window_fused(FusedArgs a, int count) {
-    extern __shared__ uint4 ring4[];  // nslots x row_stride counters
-    uint32_t* ring = reinterpret_cast<uint32_t*>(ring4);
-    __shared__ uint16_t lut[256 * kLutCopies];  // bin of each code (nbins for codes without one), per copy
-    for (int e = threadIdx.x; e < 256 * kLutCopies; e += blockDim.x) {
-        const int c = e / kLutCopies;
-        const int b = (a.k >= 1) ? (int)__ldg(&g_bin_table.bin[a.k][c]) : c;
-        lut[e] = (uint16_t)(b >= 0 ? b : a.nbins);
-    }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    extern __shared__ uint4 smem4[];  // ring (nslots x row_stride words), then staging (group x stage_words)
+    uint32_t* ring = reinterpret_cast<uint32_t*>(smem4);
     const int rs = a.row_stride, ns = a.nslots, ncp = a.ncp;
+    const uint32_t b4 = 4u * (uint32_t)ncp;  // bytes between the pair rows of a ring row
+    // per code: byte offset of its bin pair's row + 16 x (bin & 1) (codes
+    // without a compact bin: pair row nbins / 2, lower half)
+    __shared__ uint16_t lut[256];
+    for (int c = threadIdx.x; c < 256; c += kFusedThreads) {
+        int b = (a.k >= 1) ? (int)__ldg(&g_bin_table.bin[a.k][c]) : c;
+        if (b < 0) b = a.nbins;
+        lut[c] = (uint16_t)((uint32_t)(b >> 1) * b4 + 16u * (uint32_t)(b & 1));
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t ring_addr = (uint32_t)__cvta_generic_to_shared(ring);
-    const uint32_t ring_bytes = 4u * (uint32_t)(ns * rs);  // (checked builds)
-    // this lane's copy of the table: byte address of entry 0
-    const uint32_t lut_lane = (uint32_t)__cvta_generic_to_shared(lut) + 2u * (uint32_t)(lane & (kLutCopies - 1));
-    const uint32_t bin_bytes = 4u * (uint32_t)ncp;  // bytes between the bin rows of a ring row
-    const uint64_t items = (uint64_t)count * (uint64_t)a.bands;
-    for (uint64_t it = blockIdx.x; it < items; it += gridDim.x) {
-        const int img = (int)(it / (uint64_t)a.bands), band = (int)(it % (uint64_t)a.bands);
+    const uint32_t ring_bytes = 4u * (uint32_t)(ns * rs);
+    const uint32_t stage_addr = ring_addr + ring_bytes;
+    const uint32_t stage_bytes = 4u * (uint32_t)(a.group * a.stage_words);  // (checked builds)
+    const uint32_t junk_e = (uint32_t)(a.nbins >> 1) * b4;                  // table entry of the spare pair row
+    const unsigned items = (unsigned)count * (unsigned)a.bands;  // below 2^31 (checked at launch)
+    for (unsigned it = blockIdx.x; it < items; it += gridDim.x) {
+        const int img = (int)(it / (unsigned)a.bands), band = (int)(it - (unsigned)img * (unsigned)a.bands);
         const ldp_image_desc d = a.descs ? a.descs[img] : a.one;
         if (d.codes == nullptr || !win_desc_ok(d, a.max_H, a.max_W, a.status)) continue;  // uniform over the CTA
         const int H = d.H, W = d.W;
@@ -330,30 +348,38 @@ __global__ void __launch_bounds__(kFusedThreads, 4) k_window_fused(FusedArgs a, 
         const int nblk = (ncc + 31) / 32;
         const int words = nwc * a.nbins;
         uint32_t* out_img = a.hist + d.hist_offset;
-        const bool vec = (a.nbins & 3) == 0 && ((reinterpret_cast<uintptr_t>(out_img) & 15u) == 0);
+        // the staged window rows leave in 16-byte stores when the image's
+        // histograms start on a 16-byte boundary and a row is whole quads
+        const bool vec = ((reinterpret_cast<uintptr_t>(out_img) & 15u) | ((uint32_t)words & 3u)) == 0;
 
         const bool al = ((reinterpret_cast<uintptr_t>(d.codes) | (uintptr_t)d.code_pitch) & 3u) == 0;
+        int n0 = 0, sn0 = 0;  // first cell row counted by the current group, its ring slot
         // count image rows [xa, xb) of cell block cb: lane l takes cell
         // 32 cb + l (code columns s0 .. s0+n-1 of each row), each code one
-        // reduction into the ring row of its cell row
-        auto count_rows = [&](int cb, int xa, int xb, auto cw_c) {
+        // reduction into the ring row of its cell row.  COMPACT (k >= 1):
+        // code 0 has no bin, so positions past the cell's columns are zeroed
+        // and count into the spare bin row through the table; raw bins test
+        // the position instead.
+        auto count_rows = [&](int cb, int xa, int xb, auto cw_c, auto compact_c) {
             constexpr int CW = decltype(cw_c)::value;  // a.cw when it is at most 13, else 0
+            constexpr bool COMPACT = decltype(compact_c)::value;
             const int c = cb * 32 + lane;
             const int s0 = max(c * a.cw - 1, 0), e0 = min(c * a.cw + a.cw - 1, W - 2);
             const int n = c < ncc ? max(e0 - s0, 0) : 0;
-            int r = xa / a.ch;  // cell row of image row xa
-            int s = r % ns, nb = (r + 1) * a.ch;
+            const int r = (int)((unsigned)xa / (unsigned)a.ch);  // cell row of image row xa (>= n0)
+            int s = sn0 + (r - n0), nb = (r + 1) * a.ch;
+            if (s >= ns) s -= ns;
             uint32_t rb = ring_addr + 4u * (uint32_t)(s * rs + c);
-            // one code: its bin from this lane's copy of the table, one
-            // reduction (a position past the cell's columns counts into the
-            // cell's word of the spare bin row: no branch)
+            // one code (byte 0 of `code`): its table entry e, one reduction
+            // of 1 << (e mod 32) -- 1 or 1 << 16 -- at rb + (e rounded down to 32)
             auto one = [&](uint32_t code, bool ok) {
-                const uint32_t bin = ok ? (uint32_t)lut[code * kLutCopies + (lane & (kLutCopies - 1))]
-                                        : (uint32_t)a.nbins;
-                uint32_t addr;
-                asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(addr) : "r"(bin), "r"(bin_bytes), "r"(rb));
+                uint32_t e = lut[code];
+                if (!COMPACT && !ok) e = junk_e;
+                uint32_t inc;
+                asm("shf.l.wrap.b32 %0, %1, %2, %3;" : "=r"(inc) : "r"(0u), "r"(1u), "r"(e));
+                const uint32_t addr = rb + (e & ~31u);
                 if (index_ok(addr - ring_addr < ring_bytes, a.status))
-                    asm volatile("red.shared.add.u32 [%0], 1;" ::"r"(addr));
+                    asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(addr), "r"(inc));
             };
             auto next_row = [&](int x) {
                 if (x >= nb) {  // into the next cell row
@@ -363,41 +389,57 @@ __global__ void __launch_bounds__(kFusedThreads, 4) k_window_fused(FusedArgs a, 
                 }
             };
             if constexpr (CW > 0) {
-                // the cell's bytes come from four aligned words at s0 & ~3 (one
-                // row ahead) when they lie inside the row, else byte by byte
-                const int base = s0 & ~3;
+                // the cell's bytes, at positions 0 .. CW-1 from column s0,
+                // come from four aligned words at `base` (one row ahead).  With
+                // whole words (aligned code map, W - 2 >= 16) a row is read up
+                // to 16 bytes from base: past its last code into its pitch and
+                // the next row, never past the image's last code row, which
+                // (like every row without whole words) is read byte by byte,
+                // its bytes outside the cell zero
+                const int lastw = (W - 3) & ~3;             // the word holding a row's last code
+                const int base = min(s0 & ~3, lastw);       // clamped for cells past the image
                 const uint32_t sh = 8u * (uint32_t)(s0 & 3);
-                const bool words = al && base + 16 <= W - 2;
-                const uint8_t* rp = d.codes + (size_t)(xa - 1) * (size_t)d.code_pitch;
-                auto fetch = [&](const uint8_t* row, uint32_t(&w)[4]) {
-                    if (words) {
+                const bool words = al && W - 2 >= 16;       // uniform over the image
+                const int xlast = H - 2;                     // image row of the last code row
+                constexpr int NA = (CW + 3) / 4;
+                uint32_t msk[NA];                            // bytes of positions below n
 #pragma unroll
-                        for (int i = 0; i < 4; ++i) w[i] = __ldg(reinterpret_cast<const unsigned int*>(row + base) + i);
-                    } else {  // the bytes of the cell's columns only
+                for (int i = 0; i < NA; ++i) {
+                    const int m = min(max(n - 4 * i, 0), 4);
+                    msk[i] = m == 4 ? 0xFFFFFFFFu : (1u << (8 * m)) - 1u;
+                }
+                const uint8_t* rp = d.codes + (size_t)(xa - 1) * (size_t)d.code_pitch + base;
+                auto fetch = [&](const uint8_t* row, int x, uint32_t(&w)[4]) {
+                    if (words && x < xlast) {  // uniform over the warp
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) w[i] = __ldg(reinterpret_cast<const unsigned int*>(row) + i);
+                    } else {
 #pragma unroll
                         for (int i = 0; i < 4; ++i) {
                             w[i] = 0;
 #pragma unroll
                             for (int t = 0; t < 4; ++t) {
                                 const int col = base + 4 * i + t;
-                                if (col >= s0 && col < s0 + n) w[i] |= (uint32_t)__ldg(row + col) << (8 * t);
+                                if (col >= s0 && col < s0 + n) w[i] |= (uint32_t)__ldg(row + 4 * i + t) << (8 * t);
                             }
                         }
                     }
                 };
                 uint32_t w[4], nx[4];
-                if (xa < xb) fetch(rp, nx);
+                if (xa < xb) fetch(rp, xa, nx);
                 for (int x = xa; x < xb; ++x) {
 #pragma unroll
                     for (int i = 0; i < 4; ++i) w[i] = nx[i];
                     rp += d.code_pitch;
-                    if (x + 1 < xb) fetch(rp, nx);
+                    if (x + 1 < xb) fetch(rp, x + 1, nx);
                     next_row(x);
-                    // bytes j = 0 .. CW-1 of the cell at positions 4i .. 4i+3 of av[i]
-                    constexpr int NA = (CW + 3) / 4;
+                    // positions 4i .. 4i+3 in av[i]
                     uint32_t av[NA];
 #pragma unroll
-                    for (int i = 0; i < NA; ++i) av[i] = __funnelshift_r(w[i], i + 1 < 4 ? w[i + 1] : 0u, sh);
+                    for (int i = 0; i < NA; ++i) {
+                        av[i] = __funnelshift_r(w[i], i + 1 < 4 ? w[i + 1] : 0u, sh);
+                        if constexpr (COMPACT) av[i] &= msk[i];
+                    }
 #pragma unroll
                     for (int j = 0; j < CW; ++j) one(prmt(av[j >> 2], 0u, 0x4440u | (uint32_t)(j & 3)), j < n);
                 }
@@ -411,15 +453,128 @@ __global__ void __launch_bounds__(kFusedThreads, 4) k_window_fused(FusedArgs a, 
             asm volatile("" ::: "memory");  // the reductions come before the barrier that follows
         };
 
+
+        // ring slots: cell row r lives in slot r mod ns, tracked without
+        // divisions from the slot of the group's first new cell row (sn0)
+        const int ph2_ns = (2 * a.ph) % ns;
+        // output items (bin group q, block of 32 windows) go to the warps in
+        // turn: item = q * nbw + bb, stepped by the warp count
+        const bool quad = (a.nbins & 3) == 0;           // items of four bins (two pair rows), else two
+        const int nq = quad ? a.nbins >> 2 : a.nbins >> 1;
+        const int nbw = (nwc + 31) >> 5;
+        const int dbb = kFusedWarps % nbw, dq = kFusedWarps / nbw;
+        const int q_first = warp / nbw, bb_first = warp % nbw;
+
+        // the staged window rows of the previous group -> HBM
+        uint32_t* pend_dst = nullptr;
+        int pend_n = 0;  // words
+        auto copy_out = [&]() {
+            if (pend_n <= 0) return;
+            if (vec) {
+                uint4* dst = reinterpret_cast<uint4*>(pend_dst);
+                for (int e = threadIdx.x; e < (pend_n >> 2); e += kFusedThreads) {
+                    const uint32_t sa = stage_addr + 16u * (uint32_t)e;
+                    if (!index_ok(sa - stage_addr < stage_bytes, a.status)) continue;
+                    uint4 v;
+                    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                                 : "r"(sa));
+                    __stcs(dst + e, v);
+                }
+            } else {
+                for (int e = threadIdx.x; e < pend_n; e += kFusedThreads) {
+                    const uint32_t sa = stage_addr + 4u * (uint32_t)e;
+                    if (index_ok(sa - stage_addr < stage_bytes, a.status)) pend_dst[e] = lds32(sa);
+                }
+            }
+            pend_n = 0;
+        };
+
+        // window rows wa and (two) wa + 1 of the group starting at g0 into the
+        // staging copy; sw: ring slot of the first cell row of window row wa.
+        // The cell rows of both are read once, [wa * ph, wa * ph + ph + qh):
+        // the rows they share (ph < qh) count into both.
+        // QW: qw when it is a small constant (unrolled), else 0 (a loop)
+        auto emit = [&](auto qw_c, auto quad_c, int wa, bool two, int g0, int sw) {
+            constexpr int QW = decltype(qw_c)::value;
+            constexpr bool QUAD = decltype(quad_c)::value;
+            const int qwn = QW ? QW : a.qw;
+            const int nrow = min(two ? a.ph + a.qh : a.qh, ncr - wa * a.ph);
+            const uint32_t rs4 = 4u * (uint32_t)rs, so0 = rs4 * (uint32_t)sw;
+            const uint32_t st0 = stage_addr + 4u * (uint32_t)((wa - g0) * words), st1 = st0 + 4u * (uint32_t)words;
+            for (int q = q_first, bb = bb_first; q < nq;) {
+                const int b = bb * 32 + lane;  // lane l takes window 32 * block + l
+                bb += dbb;
+                const int qi = q;
+                q += dq;
+                if (bb >= nbw) {
+                    bb -= nbw;
+                    ++q;
+                }
+                if (b >= nwc) continue;
+                // pair rows (QUAD ? 2qi, 2qi+1 : qi) of cell b at p0 (p1) + so
+                const uint32_t pq = ring_addr + (QUAD ? 2u : 1u) * b4 * (uint32_t)qi + 4u * (uint32_t)b;
+                uint32_t ax = 0, ay = 0, bx = 0, by = 0;  // packed bin pairs of window rows wa, wa + 1
+                uint32_t so = so0;
+                for (int ri = 0; ri < nrow; ++ri) {
+                    const uint32_t p0 = pq + so, p1 = p0 + b4;
+                    uint32_t x = 0, y = 0;
+                    if (index_ok((QUAD ? p1 : p0) + 4u * (uint32_t)(qwn - 1) - ring_addr < ring_bytes, a.status)) {
+#pragma unroll
+                        for (int c = 0; c < qwn; ++c) {
+                            x += lds32(p0 + 4u * c);
+                            if constexpr (QUAD) y += lds32(p1 + 4u * c);
+                        }
+                    }
+                    if (ri < a.qh) {
+                        ax += x;
+                        ay += y;
+                    }
+                    if (two && ri >= a.ph) {
+                        bx += x;
+                        by += y;
+                    }
+                    so += rs4;
+                    if (so == ring_bytes) so = 0;
+                }
+                const uint32_t o = 4u * (uint32_t)(b * a.nbins + (QUAD ? 4 : 2) * qi);
+                for (int h = 0; h < (two ? 2 : 1); ++h) {
+                    const uint32_t sa = (h ? st1 : st0) + o, u = h ? bx : ax, v = h ? by : ay;
+                    if (!index_ok(sa + (QUAD ? 16u : 8u) - stage_addr <= stage_bytes, a.status)) continue;
+                    if constexpr (QUAD)
+                        asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(sa), "r"(u & 0xFFFFu),
+                                     "r"(u >> 16), "r"(v & 0xFFFFu), "r"(v >> 16)
+                                     : "memory");
+                    else
+                        asm volatile("st.shared.v2.u32 [%0], {%1, %2};" ::"r"(sa), "r"(u & 0xFFFFu), "r"(u >> 16)
+                                     : "memory");
+                }
+            }
+        };
+        auto emit_pair = [&](int wa, bool two, int g0, int sw) {
+            auto go = [&](auto quad_c) {
+                if (a.qw == 1) emit(std::integral_constant<int, 1>{}, quad_c, wa, two, g0, sw);
+                else if (a.qw == 2) emit(std::integral_constant<int, 2>{}, quad_c, wa, two, g0, sw);
+                else if (a.qw == 3) emit(std::integral_constant<int, 3>{}, quad_c, wa, two, g0, sw);
+                else if (a.qw == 4) emit(std::integral_constant<int, 4>{}, quad_c, wa, two, g0, sw);
+                else emit(std::integral_constant<int, 0>{}, quad_c, wa, two, g0, sw);
+            };
+            if (quad) go(std::true_type{});
+            else go(std::false_type{});
+        };
+
         int next = a0 * a.ph;  // first cell row not in the ring
         for (int g0 = a0; g0 < a1; g0 += a.group) {
             const int g1 = min(g0 + a.group, a1);  // window rows [g0, g1)
-            const int n0 = max(next, g0 * a.ph);
+            n0 = max(next, g0 * a.ph);
             const int n1 = min((g1 - 1) * a.ph + a.qh, ncr);  // cell rows to count: [n0, n1)
-            __syncthreads();  // the previous group's reads of the ring are done
-            for (int r = n0; r < n1; ++r) {
-                uint4* sl = reinterpret_cast<uint4*>(ring + (r % ns) * rs);
-                for (int e = threadIdx.x; e < rs / 4; e += blockDim.x) sl[e] = make_uint4(0, 0, 0, 0);
+            sn0 = n0 % ns;
+            __syncthreads();  // the previous group's reads of the ring and writes of the staging are done
+            copy_out();
+            for (int r = n0, sl = sn0; r < n1; ++r) {
+                uint4* row = reinterpret_cast<uint4*>(ring + sl * rs);
+                for (int e = threadIdx.x; e < rs / 4; e += kFusedThreads) row[e] = make_uint4(0, 0, 0, 0);
+                if (++sl == ns) sl = 0;
             }
             __syncthreads();
             if (n0 < n1) {
@@ -429,77 +584,37 @@ __global__ void __launch_bounds__(kFusedThreads, 4) k_window_fused(FusedArgs a, 
                 const int R = x1 - x0;
                 if (R > 0) {
                     const int T = R * nblk;
-                    const int t1 = (int)((int64_t)T * (warp + 1) / nwarps);
-                    for (int t = (int)((int64_t)T * warp / nwarps); t < t1;) {
-                        const int cb = t / R, r0 = t - cb * R, r1 = min(R, r0 + (t1 - t));
-                        if (a.cw == 10) count_rows(cb, x0 + r0, x0 + r1, std::integral_constant<int, 10>{});
-                        else if (a.cw <= 13) count_rows(cb, x0 + r0, x0 + r1, std::integral_constant<int, 13>{});
-                        else count_rows(cb, x0 + r0, x0 + r1, std::integral_constant<int, 0>{});
+                    const int t1 = (T * (warp + 1)) / kFusedWarps;
+                    for (int t = (T * warp) / kFusedWarps; t < t1;) {
+                        const int cb = (int)((unsigned)t / (unsigned)R), r0 = t - cb * R, r1 = min(R, r0 + (t1 - t));
+                        const int xa = x0 + r0, xb = x0 + r1;
+                        if (a.k >= 1) {
+                            const std::true_type cp;
+                            if (a.cw == 10) count_rows(cb, xa, xb, std::integral_constant<int, 10>{}, cp);
+                            else if (a.cw <= 13) count_rows(cb, xa, xb, std::integral_constant<int, 13>{}, cp);
+                            else count_rows(cb, xa, xb, std::integral_constant<int, 0>{}, cp);
+                        } else {
+                            const std::false_type cp;
+                            if (a.cw <= 13) count_rows(cb, xa, xb, std::integral_constant<int, 13>{}, cp);
+                            else count_rows(cb, xa, xb, std::integral_constant<int, 0>{}, cp);
+                        }
                         t += r1 - r0;
                     }
                 }
             }
             next = max(next, n1);
             __syncthreads();
-            for (int wa = g0; wa < g1; ++wa) {
-                const int r0 = wa * a.ph, nr = min(a.qh, ncr - r0), s0 = r0 % ns;
-                uint32_t* out = out_img + (uint64_t)wa * (uint64_t)words;
-                // items (bin group q, block of 32 windows): lane l takes window
-                // 32 * block + l, so a warp's loads read 32 consecutive cells of
-                // one bin row (32 banks); the warps take items in turn
-                const int nq = vec ? a.nbins / 4 : a.nbins;
-                const int nbw = (nwc + 31) / 32;
-                // QW: qw when it is a small constant (unrolled), else 0 (a loop)
-                auto emit = [&](auto qw_c) {
-                    constexpr int QW = decltype(qw_c)::value;
-                    // item = (q, block bb) = q * nbw + bb, stepped by the warp count
-                    const int dbb = nwarps % nbw, dq = nwarps / nbw;
-                    for (int q = warp / nbw, bb = warp % nbw; q < nq;) {
-                        const int b = bb * 32 + lane;
-                        bb += dbb;
-                        const int qi = q;
-                        q += dq;
-                        if (bb >= nbw) {
-                            bb -= nbw;
-                            ++q;
-                        }
-                        if (b >= nwc) continue;
-                        if (vec) {
-                            uint4 acc = make_uint4(0, 0, 0, 0);
-                            int sidx = s0;
-                            for (int ri = 0; ri < nr; ++ri) {
-                                const uint32_t* rw = ring + sidx * rs + 4 * qi * ncp + b;
-#pragma unroll
-                                for (int c = 0; c < (QW ? QW : a.qw); ++c) {
-                                    if (!index_ok(sidx * rs + (4 * qi + 3) * ncp + b + c < ns * rs, a.status)) continue;
-                                    acc.x += rw[c];
-                                    acc.y += rw[c + ncp];
-                                    acc.z += rw[c + 2 * ncp];
-                                    acc.w += rw[c + 3 * ncp];
-                                }
-                                if (++sidx == ns) sidx = 0;
-                            }
-                            __stcs(reinterpret_cast<uint4*>(out + (size_t)b * a.nbins + 4 * qi), acc);
-                        } else {
-                            uint32_t acc = 0;
-                            int sidx = s0;
-                            for (int ri = 0; ri < nr; ++ri) {
-                                const uint32_t* rw = ring + sidx * rs + qi * ncp + b;
-                                for (int c = 0; c < (QW ? QW : a.qw); ++c)
-                                    if (index_ok(sidx * rs + qi * ncp + b + c < ns * rs, a.status)) acc += rw[c];
-                                if (++sidx == ns) sidx = 0;
-                            }
-                            out[(size_t)b * a.nbins + qi] = acc;
-                        }
-                    }
-                };
-                if (a.qw == 1) emit(std::integral_constant<int, 1>{});
-                else if (a.qw == 2) emit(std::integral_constant<int, 2>{});
-                else if (a.qw == 3) emit(std::integral_constant<int, 3>{});
-                else if (a.qw == 4) emit(std::integral_constant<int, 4>{});
-                else emit(std::integral_constant<int, 0>{});
+            int sw = (g0 * a.ph) % ns;  // slot of the first cell row of window row wa
+            for (int wa = g0; wa < g1; wa += 2) {
+                emit_pair(wa, wa + 1 < g1, g0, sw);
+                sw += ph2_ns;
+                if (sw >= ns) sw -= ns;
             }
+            pend_dst = out_img + (size_t)g0 * (size_t)words;
+            pend_n = (g1 - g0) * words;
         }
+        __syncthreads();
+        copy_out();
     }
 }
 
@@ -517,21 +632,24 @@ int gcd_int(int a, int b) {
 bool window_direct(const WindowGeom& g) { return g.wh == g.sh && g.ww == g.sw; }
 
 namespace {
-// The fused pass for images up to max_W wide: ring row words (rs), window
-// rows per group (G) and ring rows (nslots); rs = 0 when the pass does not
-// apply (stride = size, a column stride that does not divide the width, or
-// rows of cells too wide for shared memory).  Groups take as many window
-// rows as keep the ring within kFusedGroupWords (up to kFusedMaxGroup); rows
-// of windows with gaps between them (row stride above the height) are not
-// grouped.
 struct FusedPlan {
     uint64_t rs = 0;
-    int ncp = 0, group = 1, nslots = 1;
+    int ncp = 0, group = 1, nslots = 1, stage_words = 0;
 };
 
+// The fused pass for images up to max_W wide: ring row words (rs), staging
+// words per window row, window rows per group (G) and ring rows (nslots);
+// rs = 0 when the pass does not apply (stride = size, a column stride that
+// does not divide the width, windows of more than 65535 pixels -- their sums
+// would not fit a 16-bit half --, table offsets past 16 bits, or rows of cells
+// too wide for shared memory).  Groups take as many window rows as keep the
+// ring and the staging within kFusedGroupWords (up to kFusedMaxGroup); rows of
+// windows with gaps between them (row stride above the height) are not
+// grouped.
 FusedPlan fused_plan(int max_W, const WindowGeom& g) {
     FusedPlan p;
-    if (window_direct(g) || g.ww % g.sw != 0) return p;
+    if (window_direct(g) || g.ww % g.sw != 0 || (g.nbins & 1) != 0) return p;
+    if ((int64_t)g.wh * (int64_t)g.ww > 65535) return p;
     const int ch = gcd_int(g.wh, g.sh), qh = g.wh / ch, qw = g.ww / g.sw, ph = g.sh / ch;
     // cells of a ring row: those a window row reads (the last window of the
     // widest image starts in cell nwc - 1 and spans qw cells) and those
@@ -539,15 +657,18 @@ FusedPlan fused_plan(int max_W, const WindowGeom& g) {
     const int nwc = max_W <= g.ww ? 1 : (max_W - g.ww + g.sw - 1) / g.sw + 1;
     const int ncells = std::max(nwc + qw - 1, (max_W - 2) / g.sw + 1);
     const int ncp = (ncells + 31) / 32 * 32;
-    const uint64_t rs = (uint64_t)(g.nbins + 1) * (uint64_t)ncp;
-    if ((uint64_t)qh * rs > (uint64_t)kFusedSmemWords) return p;
+    if ((uint64_t)(g.nbins / 2) * 4u * (uint64_t)ncp + 16u > 65535u) return p;
+    const uint64_t rs = (uint64_t)(g.nbins / 2 + 1) * (uint64_t)ncp;
+    const uint64_t stage = (uint64_t)nwc * (uint64_t)g.nbins;
+    if ((uint64_t)qh * rs + stage > (uint64_t)kFusedSmemWords) return p;
     p.rs = rs;
     p.ncp = ncp;
     p.nslots = qh;
+    p.stage_words = (int)stage;
     if (ph <= qh)
         for (int G = 2; G <= kFusedMaxGroup; ++G) {
             const int ns = (G - 1) * ph + qh;
-            if ((uint64_t)ns * rs > (uint64_t)kFusedGroupWords) break;
+            if ((uint64_t)ns * rs + (uint64_t)G * stage > (uint64_t)kFusedGroupWords) break;
             p.group = G;
             p.nslots = ns;
         }
@@ -590,6 +711,7 @@ cudaError_t launch_windows(const ldp_image_desc* d_descs, const ldp_image_desc* 
         fa.nbins = g.nbins;
         fa.k = g.compact ? g.k : 0;
         fa.row_stride = (int)fp.rs;
+        fa.stage_words = fp.stage_words;
         fa.ncp = fp.ncp;
         fa.group = fp.group;
         fa.nslots = fp.nslots;
@@ -597,7 +719,8 @@ cudaError_t launch_windows(const ldp_image_desc* d_descs, const ldp_image_desc* 
         fa.max_H = max_H;
         fa.max_W = max_W;
         fa.status = status;
-        const size_t smem = sizeof(uint32_t) * (size_t)fp.rs * (size_t)fp.nslots;
+        const size_t smem =
+            sizeof(uint32_t) * ((size_t)fp.rs * (size_t)fp.nslots + (size_t)fp.group * (size_t)fp.stage_words);
         int occ = 0;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_window_fused, kFusedThreads, smem);
         if (e != cudaSuccess) return e;
@@ -610,6 +733,7 @@ cudaError_t launch_windows(const ldp_image_desc* d_descs, const ldp_image_desc* 
         const int max_bands = (nwr_max + fp.group - 1) / fp.group;
         if (bands > max_bands) bands = max_bands;
         if (bands < 1) bands = 1;
+        if ((int64_t)count * bands > (int64_t)INT32_MAX) bands = 1;  // work items stay below 2^31
         fa.rows_per_band = (nwr_max + bands - 1) / bands;
         fa.bands = (nwr_max + fa.rows_per_band - 1) / fa.rows_per_band;
         const uint64_t items = (uint64_t)count * (uint64_t)fa.bands;

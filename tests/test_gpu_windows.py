@@ -42,6 +42,9 @@ def _h(t):
     (57, 1030, (4, 9), (2, 3)),       # fused: 344 cells per ring row
     (50, 60, (80, 80), (40, 40)),     # fused: one window, larger than the image
     (30, 30, (64, 64), (16, 16)),     # fused: a window wider than the image's cells (zero cells past it)
+    (45, 18, (10, 10), (5, 5)),       # fused: rows of 16 codes (the narrowest read in whole words)
+    (40, 14, (6, 4), (3, 2)),         # fused: rows of 12 codes (aligned, read byte by byte)
+    (31, 642, (20, 20), (10, 10)),    # fused: 640 codes a row, cells of ten columns in whole words
 ])
 def test_single_image_windows(env, H, W, window, stride):
     torch, ldp, oracle, synth = env
