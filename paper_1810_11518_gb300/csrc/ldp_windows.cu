@@ -281,7 +281,7 @@ struct FusedArgs {
     int nbins, k;        // as in CellArgs (nbins even)
     int ncp;             // cells per ring row: a multiple of 32 covering the widest image's cells and windows
     int row_stride;      // ring words per cell row: (nbins / 2 + 1) x ncp (bin pairs, pair nbins / 2 takes codes without a bin)
-    int stage_words;     // staging words per window row: the widest image's windows x nbins
+    int stage_words;     // staging words per window row: the widest image's windows x their stride in the staging
     int group;           // window rows per group (G)
     int nslots;          // ring rows: (G - 1) * ph + qh
     int rows_per_band;   // window rows per work item
@@ -334,6 +334,16 @@ __global__ void __launch_bounds__(kFusedThreads, 4) k_window_fused(FusedArgs a, 
     const uint32_t stage_addr = ring_addr + ring_bytes;
     const uint32_t stage_bytes = 4u * (uint32_t)(a.group * a.stage_words);  // (checked builds)
     const uint32_t junk_e = (uint32_t)(a.nbins >> 1) * b4;                  // table entry of the spare pair row
+    // staging: window rows of windows S words apart (nbins, padded by four
+    // words when nbins is a multiple of 8, so that the 16-byte stores of 8
+    // consecutive windows fall in 32 different banks); the copy to HBM
+    // drops the padding: thread t's first 16-byte chunk and its step, as
+    // (window, chunk in window) pairs packed into bytes
+    const int S = (a.nbins & 7) == 0 ? a.nbins + 4 : a.nbins;
+    const int nq4 = a.nbins >> 2;
+    const uint32_t cpk = nq4 == 0 ? 0u
+                                  : (uint32_t)(threadIdx.x / nq4) | (uint32_t)(threadIdx.x % nq4) << 8 |
+                                        (uint32_t)(kFusedThreads / nq4) << 16 | (uint32_t)(kFusedThreads % nq4) << 24;
     const unsigned items = (unsigned)count * (unsigned)a.bands;  // below 2^31 (checked at launch)
     for (unsigned it = blockIdx.x; it < items; it += gridDim.x) {
         const int img = (int)(it / (unsigned)a.bands), band = (int)(it - (unsigned)img * (unsigned)a.bands);
@@ -349,8 +359,9 @@ __global__ void __launch_bounds__(kFusedThreads, 4) k_window_fused(FusedArgs a, 
         const int words = nwc * a.nbins;
         uint32_t* out_img = a.hist + d.hist_offset;
         // the staged window rows leave in 16-byte stores when the image's
-        // histograms start on a 16-byte boundary and a row is whole quads
-        const bool vec = ((reinterpret_cast<uintptr_t>(out_img) & 15u) | ((uint32_t)words & 3u)) == 0;
+        // histograms start on a 16-byte boundary and every window is whole
+        // quads of bins (the staging copy is read by windows)
+        const bool vec = (a.nbins & 3) == 0 && (reinterpret_cast<uintptr_t>(out_img) & 15u) == 0;
 
         const bool al = ((reinterpret_cast<uintptr_t>(d.codes) | (uintptr_t)d.code_pitch) & 3u) == 0;
         int n0 = 0, sn0 = 0;  // first cell row counted by the current group, its ring slot
@@ -472,8 +483,16 @@ __global__ void __launch_bounds__(kFusedThreads, 4) k_window_fused(FusedArgs a, 
             if (pend_n <= 0) return;
             if (vec) {
                 uint4* dst = reinterpret_cast<uint4*>(pend_dst);
+                int wi = (int)(cpk & 0xFFu), j = (int)(cpk >> 8 & 0xFFu);
+                const int dw = (int)(cpk >> 16 & 0xFFu), dj = (int)(cpk >> 24);
                 for (int e = threadIdx.x; e < (pend_n >> 2); e += kFusedThreads) {
-                    const uint32_t sa = stage_addr + 16u * (uint32_t)e;
+                    const uint32_t sa = stage_addr + 4u * (uint32_t)(wi * S + 4 * j);
+                    wi += dw;
+                    j += dj;
+                    if (j >= nq4) {
+                        j -= nq4;
+                        ++wi;
+                    }
                     if (!index_ok(sa - stage_addr < stage_bytes, a.status)) continue;
                     uint4 v;
                     asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
@@ -483,7 +502,8 @@ __global__ void __launch_bounds__(kFusedThreads, 4) k_window_fused(FusedArgs a, 
                 }
             } else {
                 for (int e = threadIdx.x; e < pend_n; e += kFusedThreads) {
-                    const uint32_t sa = stage_addr + 4u * (uint32_t)e;
+                    const int wi = e / a.nbins;  // (unaligned histograms only)
+                    const uint32_t sa = stage_addr + 4u * (uint32_t)(wi * S + (e - wi * a.nbins));
                     if (index_ok(sa - stage_addr < stage_bytes, a.status)) pend_dst[e] = lds32(sa);
                 }
             }
@@ -501,7 +521,8 @@ __global__ void __launch_bounds__(kFusedThreads, 4) k_window_fused(FusedArgs a, 
             const int qwn = QW ? QW : a.qw;
             const int nrow = min(two ? a.ph + a.qh : a.qh, ncr - wa * a.ph);
             const uint32_t rs4 = 4u * (uint32_t)rs, so0 = rs4 * (uint32_t)sw;
-            const uint32_t st0 = stage_addr + 4u * (uint32_t)((wa - g0) * words), st1 = st0 + 4u * (uint32_t)words;
+            const uint32_t srow = 4u * (uint32_t)(nwc * S);  // staging bytes per window row
+            const uint32_t st0 = stage_addr + srow * (uint32_t)(wa - g0), st1 = st0 + srow;
             for (int q = q_first, bb = bb_first; q < nq;) {
                 const int b = bb * 32 + lane;  // lane l takes window 32 * block + l
                 bb += dbb;
@@ -537,7 +558,7 @@ __global__ void __launch_bounds__(kFusedThreads, 4) k_window_fused(FusedArgs a, 
                     so += rs4;
                     if (so == ring_bytes) so = 0;
                 }
-                const uint32_t o = 4u * (uint32_t)(b * a.nbins + (QUAD ? 4 : 2) * qi);
+                const uint32_t o = 4u * (uint32_t)(b * S + (QUAD ? 4 : 2) * qi);
                 for (int h = 0; h < (two ? 2 : 1); ++h) {
                     const uint32_t sa = (h ? st1 : st0) + o, u = h ? bx : ax, v = h ? by : ay;
                     if (!index_ok(sa + (QUAD ? 16u : 8u) - stage_addr <= stage_bytes, a.status)) continue;
@@ -659,7 +680,9 @@ FusedPlan fused_plan(int max_W, const WindowGeom& g) {
     const int ncp = (ncells + 31) / 32 * 32;
     if ((uint64_t)(g.nbins / 2) * 4u * (uint64_t)ncp + 16u > 65535u) return p;
     const uint64_t rs = (uint64_t)(g.nbins / 2 + 1) * (uint64_t)ncp;
-    const uint64_t stage = (uint64_t)nwc * (uint64_t)g.nbins;
+    // staging words per window row: windows (g.nbins + 4) words apart when
+    // nbins is a multiple of 8 (bank spread of the 16-byte stores)
+    const uint64_t stage = (uint64_t)nwc * (uint64_t)(g.nbins % 8 == 0 ? g.nbins + 4 : g.nbins);
     if ((uint64_t)qh * rs + stage > (uint64_t)kFusedSmemWords) return p;
     p.rs = rs;
     p.ncp = ncp;
