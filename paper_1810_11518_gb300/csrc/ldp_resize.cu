@@ -28,6 +28,28 @@ namespace {
 constexpr int kRows = 64;
 constexpr int kThreads = 256;
 constexpr int kMaxCols = 4096;     // output widths whose column table fits in shared memory
+constexpr int kMaxFastCols = 2048;  // output widths with the per-group word tables
+
+__device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
+    uint32_t d;
+    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(sel));
+    return d;
+}
+
+// a.lo * b.byte0 + a.hi * b.byte1 + c (16-bit weights, 8-bit pixels)
+__device__ __forceinline__ uint32_t dp2a_lo(uint32_t a, uint32_t b, uint32_t c) {
+    uint32_t d;
+    asm("dp2a.lo.u32.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+
+// Bytes o_t (t = 0..3, each below 16) of the 16 bytes w[0..3], one per byte
+// lane: selector nibble t = o_t mod 8 picks from w[0..1] and from w[2..3],
+// the byte mask m (0xFF in lane t where o_t >= 8) chooses between them.
+__device__ __forceinline__ uint32_t pick16(const uint32_t (&w)[4], uint32_t sel, uint32_t m) {
+    const uint32_t lo = prmt(w[0], w[1], sel), hi = prmt(w[2], w[3], sel);
+    return (lo & ~m) | (hi & m);
+}
 
 __device__ __forceinline__ void coord(int i, int n_src, int n_dst, int& i0, int& w1) {
     // y = num / den with num = (2i + 1) n_src - n_dst, den = 2 n_dst
@@ -89,6 +111,12 @@ __global__ void __launch_bounds__(kThreads) k_resize(ResizeArgs a) {
     __shared__ const uint8_t* s_pb[kRows];
     __shared__ uint32_t s_wy1[kRows];
     __shared__ uint32_t s_col[kMaxCols];  // x0 << 12 | wx1 of each output column (OW <= kMaxCols)
+    // OW <= kMaxFastCols: per column wx0 | wx1 << 16; per group of four
+    // columns: source column B of the aligned word the group's bytes start
+    // in (bit 31: they end within 16 bytes of it), the byte selectors of the
+    // four left (low half) and right (high half) neighbours, their masks
+    __shared__ uint32_t s_wp[kMaxFastCols];
+    __shared__ uint32_t s_grp[kMaxFastCols];
     const int r0 = blockIdx.x * kRows;
     const bool table = a.OW <= kMaxCols;
     for (int img = blockIdx.y; img < a.count; img += gridDim.y) {
@@ -99,6 +127,11 @@ __global__ void __launch_bounds__(kThreads) k_resize(ResizeArgs a) {
             if (threadIdx.x == 0 && blockIdx.x == 0) atomicOr(a.status, kStatusBadCrop);
             continue;
         }
+        // word path: aligned source rows of at least 16 bytes; a group reads
+        // the 16 bytes from its aligned start B, which may run past W into
+        // the row's pitch and the next row, so rows that are the image's last
+        // take the byte gathers
+        const bool fast = a.OW <= kMaxFastCols && (((uintptr_t)d.src | (uintptr_t)d.pitch) & 3u) == 0 && d.W >= 16;
         __syncthreads();  // the previous image's tables are no longer read
         if (threadIdx.x < kRows && r0 + (int)threadIdx.x < a.OH) {
             int y0, w;
@@ -106,9 +139,37 @@ __global__ void __launch_bounds__(kThreads) k_resize(ResizeArgs a) {
             const int y1 = y0 + 1 < d.ch ? y0 + 1 : y0;
             s_pa[threadIdx.x] = d.src + (size_t)(d.cy + y0) * (size_t)d.pitch + d.cx;
             s_pb[threadIdx.x] = d.src + (size_t)(d.cy + y1) * (size_t)d.pitch + d.cx;
-            s_wy1[threadIdx.x] = (uint32_t)w;
+            s_wy1[threadIdx.x] = (uint32_t)w | (fast && d.cy + y1 < d.H - 1 ? 0x80000000u : 0u);
         }
-        if (table)
+        if (fast)
+            for (int g = threadIdx.x; 4 * g < a.OW; g += blockDim.x) {
+                int x0[4], xb[4];
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const int j = min(4 * g + t, a.OW - 1);
+                    int wx1;
+                    coord(j, d.cw, a.OW, x0[t], wx1);
+                    xb[t] = x0[t] + 1 < d.cw ? x0[t] + 1 : x0[t];
+                    if (4 * g + t < a.OW) {
+                        s_col[j] = ((uint32_t)x0[t] << 12) | (uint32_t)wx1;
+                        s_wp[j] = (2048u - (uint32_t)wx1) | ((uint32_t)wx1 << 16);
+                    }
+                }
+                const int B = (d.cx + x0[0]) & ~3;
+                uint32_t sel = 0, mL = 0, mR = 0;
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const int oL = min(d.cx + x0[t] - B, 15), oR = min(d.cx + xb[t] - B, 15);
+                    sel |= ((uint32_t)(oL & 7) << (4 * t)) | ((uint32_t)(oR & 7) << (16 + 4 * t));
+                    mL |= (oL >= 8 ? 0xFFu : 0u) << (8 * t);
+                    mR |= (oR >= 8 ? 0xFFu : 0u) << (8 * t);
+                }
+                s_grp[4 * (g & 511)] = (uint32_t)B | (d.cx + xb[3] - B < 16 ? 0x80000000u : 0u);
+                s_grp[4 * (g & 511) + 1] = sel;
+                s_grp[4 * (g & 511) + 2] = mL;
+                s_grp[4 * (g & 511) + 3] = mR;
+            }
+        else if (table)
             for (int j = threadIdx.x; j < a.OW; j += blockDim.x) {
                 int x0, wx1;
                 coord(j, d.cw, a.OW, x0, wx1);
@@ -137,12 +198,47 @@ __global__ void __launch_bounds__(kThreads) k_resize(ResizeArgs a) {
             for (; r < nr;) {
                 const uint8_t* pa = s_pa[r];
                 const uint8_t* pb = s_pb[r];
-                const uint32_t wy1 = s_wy1[r];
+                const uint32_t wyf = s_wy1[r], wy1 = wyf & 0xFFFu;
                 const int j0 = 4 * cg;
                 uint8_t* dp = drow + (size_t)r * (size_t)d.dst_pitch + j0;
                 if (j0 + 4 <= a.OW) {
-                    const uint32_t v0 = pixel(pa, pb, wy1, j0), v1 = pixel(pa, pb, wy1, j0 + 1);
-                    const uint32_t v2 = pixel(pa, pb, wy1, j0 + 2), v3 = pixel(pa, pb, wy1, j0 + 3);
+                    uint32_t v0, v1, v2, v3;
+                    const uint32_t gB = fast ? s_grp[4 * (cg & 511)] : 0u;
+                    if ((wyf & gB) >> 31) {
+                        // the group's source bytes lie in four aligned words
+                        // of each row: gather them with byte permutes, one
+                        // dp2a per row and pixel
+                        const int B = (int)(gB & 0x7FFFFFFFu);
+                        const uint32_t sel = s_grp[4 * (cg & 511) + 1], mL = s_grp[4 * (cg & 511) + 2],
+                                       mR = s_grp[4 * (cg & 511) + 3];
+                        const unsigned int* qa = reinterpret_cast<const unsigned int*>(pa - d.cx + B);
+                        const unsigned int* qb = reinterpret_cast<const unsigned int*>(pb - d.cx + B);
+                        uint32_t wa[4], wb[4];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            wa[i] = __ldg(qa + i);
+                            wb[i] = __ldg(qb + i);
+                        }
+                        const uint32_t la = pick16(wa, sel & 0xFFFFu, mL), ra = pick16(wa, sel >> 16, mR);
+                        const uint32_t lb = pick16(wb, sel & 0xFFFFu, mL), rb = pick16(wb, sel >> 16, mR);
+                        uint32_t v[4];
+#pragma unroll
+                        for (int t = 0; t < 4; ++t) {
+                            const uint32_t wp = s_wp[j0 + t], ps = (uint32_t)t | ((uint32_t)(4 + t) << 4);
+                            const uint32_t top = dp2a_lo(wp, prmt(la, ra, ps), 0u);
+                            const uint32_t bot = dp2a_lo(wp, prmt(lb, rb, ps), 0u);
+                            v[t] = ((2048u - wy1) * top + wy1 * bot + (1u << 21)) >> 22;
+                        }
+                        v0 = v[0];
+                        v1 = v[1];
+                        v2 = v[2];
+                        v3 = v[3];
+                    } else {
+                        v0 = pixel(pa, pb, wy1, j0);
+                        v1 = pixel(pa, pb, wy1, j0 + 1);
+                        v2 = pixel(pa, pb, wy1, j0 + 2);
+                        v3 = pixel(pa, pb, wy1, j0 + 3);
+                    }
                     if (words) {
                         *reinterpret_cast<uint32_t*>(dp) = v0 | (v1 << 8) | (v2 << 16) | (v3 << 24);
                     } else {
@@ -173,7 +269,7 @@ __global__ void __launch_bounds__(kThreads) k_resize(ResizeArgs a) {
                     const uint8_t* pb = s_pb[rr];
                     const uint32_t top = wx0 * __ldg(pa + x0) + (uint32_t)wx1 * __ldg(pa + xb);
                     const uint32_t bot = wx0 * __ldg(pb + x0) + (uint32_t)wx1 * __ldg(pb + xb);
-                    const uint32_t wy1 = s_wy1[rr];
+                    const uint32_t wy1 = s_wy1[rr] & 0xFFFu;
                     const uint32_t v = (2048u - wy1) * top + wy1 * bot;
                     *dp = (uint8_t)((v + (1u << 21)) >> 22);
                 }

@@ -32,6 +32,9 @@ def env():
     ((1, 1), None, (4, 300)),
     ((6, 9), None, (3, 4101)),                  # wider than the column table
     ((300, 200), (0, 0, 300, 199), (130, 4096)),  # widest output with the table
+    ((20, 32), None, (41, 97)),                 # aligned rows, upsampling (source words)
+    ((90, 400), None, (30, 130)),               # aligned rows, about 3x down (source words)
+    ((60, 512), (0, 1, 60, 509), (15, 126)),    # about 4x down: groups past 16 bytes gather bytes
 ])
 def test_resize_parity(env, shape, crop, out_hw):
     torch, ldp, oracle, synth = env
