@@ -11,9 +11,14 @@
 // widths up to kMaxCols) every column's coordinate, are computed once into
 // shared memory, in 32-bit arithmetic whenever the numbers fit.  Threads then
 // take groups of four output columns of the rows in turn (the CTA's work
-// spread evenly whatever the width), gather the sixteen source bytes and
-// store the four results as one 32-bit word where the destination allows.
-// Wider outputs compute their column coordinates per thread instead.
+// spread evenly whatever the width) and store the four results as one
+// 32-bit word where the destination allows.  With aligned source rows (and
+// outputs up to kMaxFastCols wide) a group whose source bytes lie within 16
+// bytes of an aligned word reads four words of each of its two source rows,
+// picks its eight left and right neighbours with byte permutes and forms each
+// row's weighted sum with one dp2a (two 16-bit weights times two bytes); other
+// groups, and rows that are the image's last, gather the sixteen bytes one by
+// one.  Wider outputs compute their column coordinates per thread instead.
 #include <cuda_runtime.h>
 
 #include <cstdint>
