@@ -36,6 +36,7 @@ namespace {
 
 constexpr int kCellThreads = 256;
 constexpr int kCellSmemWords = 12156;  // counters at most: with 4 junk words and the 512-byte table, 48 KB
+constexpr int kCellThreadSmemBytes = 45056;  // thread-per-cell counters at most (44 KB)
 
 struct CellArgs {
     const ldp_image_desc* descs;  // nullptr: the single image `one`
@@ -203,6 +204,132 @@ __global__ void __launch_bounds__(kCellThreads) k_cell_hist_image(CellArgs a, in
         uint32_t* out = a.direct ? a.hist + d.hist_offset : a.cells + (uint64_t)img * a.cell_stride;
         if (a.direct || index_ok((uint64_t)words <= a.cell_stride, a.status))
             for (int e = threadIdx.x; e < words; e += blockDim.x) out[e] = cnt[e];
+    }
+}
+
+// Whole-image items with a thread per cell, for images whose cells fit one
+// CTA's threads and whose counters fit shared memory (the face-sized crops):
+// counters are 16 bits, two bins to a word, pair-major with the cell index
+// fastest -- bin j of cell c is half j & 1 of word (j >> 1) * P + c, P a
+// multiple of 32 -- so the 32 reductions of a warp (32 consecutive cells)
+// hit 32 different banks whatever the codes.  A cell holds at most 65535
+// pixels.  Each thread walks its cell's rows: cells of CW columns read
+// aligned words one row ahead (rows above the image's last code row may be
+// read into their pitch and the next row) and cut them into bytes with a
+// funnel shift, positions past the cell masked to code 0 (no compact bin:
+// the spare pair row); other cell widths, unaligned code maps and the last
+// code row read byte by byte.  The counters then leave as the cells'
+// histograms, four bins per 16-byte store where the output allows.
+template <int CW>
+__device__ __forceinline__ void count_cell(const ldp_image_desc& d, const CellArgs& a, int cell, int ncc, int P,
+                                           uint32_t cnt_addr, uint32_t cnt_bytes, const uint16_t* lut,
+                                           uint32_t junk_e, bool al) {
+    const int H = d.H, W = d.W;
+    const int cr = cell / ncc, cc = cell - cr * ncc;
+    const int xlo = max(cr * a.ch, 1), xhi = min(cr * a.ch + a.ch, H - 1);  // image rows with codes
+    const int ylo = max(cc * a.cw, 1), yhi = min(cc * a.cw + a.cw, W - 1);
+    const int s0 = ylo - 1, n = max(yhi - ylo, 0);                          // code columns s0 .. s0+n-1
+    const uint32_t rb = cnt_addr + 4u * (uint32_t)cell;
+    auto one = [&](uint32_t code, bool ok) {
+        uint32_t e = lut[code];
+        if (!ok) e = junk_e;
+        uint32_t inc;
+        asm("shf.l.wrap.b32 %0, %1, %2, %3;" : "=r"(inc) : "r"(0u), "r"(1u), "r"(e));
+        const uint32_t addr = rb + (e & ~31u);
+        if (index_ok(addr - cnt_addr < cnt_bytes, a.status)) asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(addr), "r"(inc));
+    };
+    const uint8_t* rp = d.codes + (size_t)(xlo - 1) * (size_t)d.code_pitch;
+    constexpr int NW = CW > 0 ? (CW + 6) / 4 : 1;  // words holding CW bytes from any byte offset
+    if constexpr (CW > 0) {
+        const int base = s0 & ~3;
+        const uint32_t sh = 8u * (uint32_t)(s0 & 3);
+        const bool words = al && W - 2 >= 4 * NW;  // uniform over the image
+        const bool compact = a.k >= 1;             // code 0 has no bin
+        constexpr int NA = (CW + 3) / 4;
+        for (int x = xlo; x < xhi; ++x, rp += d.code_pitch) {
+            uint32_t w[NW];
+            if (words && x < H - 2) {
+#pragma unroll
+                for (int i = 0; i < NW; ++i) w[i] = __ldg(reinterpret_cast<const unsigned int*>(rp + base) + i);
+            } else {
+#pragma unroll
+                for (int i = 0; i < NW; ++i) {
+                    w[i] = 0;
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        const int col = base + 4 * i + t;
+                        if (col >= s0 && col < s0 + n) w[i] |= (uint32_t)__ldg(rp + col) << (8 * t);
+                    }
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < NA; ++i) {
+                uint32_t av = __funnelshift_r(w[i], i + 1 < NW ? w[i + 1] : 0u, sh);
+                const int m = min(max(n - 4 * i, 0), 4);  // positions below n in this word
+                if (compact) av &= m == 4 ? 0xFFFFFFFFu : (1u << (8 * m)) - 1u;
+#pragma unroll
+                for (int t = 0; t < 4; ++t)
+                    if (4 * i + t < CW) one(prmt(av, 0u, 0x4440u | (uint32_t)t), compact || 4 * i + t < n);
+            }
+        }
+    } else {
+        for (int x = xlo; x < xhi; ++x, rp += d.code_pitch)
+            for (int j = 0; j < n; ++j) one(__ldg(rp + s0 + j), true);
+    }
+}
+
+__global__ void __launch_bounds__(kCellThreads) k_cell_hist_thread(CellArgs a, int count, int P) {
+    extern __shared__ uint4 cnt4[];  // (nbins / 2 + 1) x P words
+    uint32_t* cnt = reinterpret_cast<uint32_t*>(cnt4);
+    const int npr = a.nbins / 2 + 1;
+    const uint32_t cnt_addr = (uint32_t)__cvta_generic_to_shared(cnt);
+    const uint32_t cnt_bytes = 4u * (uint32_t)(npr * P);
+    // per code: byte offset of its bin pair's row + 16 x (bin & 1) (codes
+    // without a compact bin: pair row nbins / 2, lower half)
+    __shared__ uint16_t lut[256];
+    for (int c = threadIdx.x; c < 256; c += blockDim.x) {
+        int b = (a.k >= 1) ? (int)__ldg(&g_bin_table.bin[a.k][c]) : c;
+        if (b < 0) b = a.nbins;
+        lut[c] = (uint16_t)((uint32_t)(b >> 1) * 4u * (uint32_t)P + 16u * (uint32_t)(b & 1));
+    }
+    const uint32_t junk_e = (uint32_t)(a.nbins >> 1) * 4u * (uint32_t)P;
+    for (int img = blockIdx.x; img < count; img += gridDim.x) {
+        const ldp_image_desc d = desc_of(a, img);
+        if (d.codes == nullptr || !win_desc_ok(d, a.max_H, a.max_W, a.status)) continue;  // uniform over the CTA
+        const int ncc = (d.W + a.cw - 1) / a.cw, ncells = ((d.H + a.ch - 1) / a.ch) * ncc;
+        __syncthreads();  // table ready; the previous image's counters are stored
+        for (int e = threadIdx.x; e < npr * P / 4; e += blockDim.x) cnt4[e] = make_uint4(0, 0, 0, 0);
+        __syncthreads();
+        const bool al = (((uintptr_t)d.codes | (uintptr_t)d.code_pitch) & 3u) == 0;
+        for (int cell = threadIdx.x; cell < ncells; cell += blockDim.x) {
+            if (a.cw == 20) count_cell<20>(d, a, cell, ncc, P, cnt_addr, cnt_bytes, lut, junk_e, al);
+            else if (a.cw == 10) count_cell<10>(d, a, cell, ncc, P, cnt_addr, cnt_bytes, lut, junk_e, al);
+            else if (a.cw == 25) count_cell<25>(d, a, cell, ncc, P, cnt_addr, cnt_bytes, lut, junk_e, al);
+            else count_cell<0>(d, a, cell, ncc, P, cnt_addr, cnt_bytes, lut, junk_e, al);
+        }
+        asm volatile("" ::: "memory");
+        __syncthreads();
+        // cell c's histogram: words c * nbins .. of its output; thread per
+        // (cell, group of four bins), cells fastest (conflict-free reads)
+        uint32_t* out = a.direct ? a.hist + d.hist_offset : a.cells + (uint64_t)img * a.cell_stride;
+        const int words = ncells * a.nbins;
+        if (!a.direct && !index_ok((uint64_t)words <= a.cell_stride, a.status)) continue;
+        const bool vec = (a.nbins & 3) == 0 && (reinterpret_cast<uintptr_t>(out) & 15u) == 0;
+        if (vec) {
+            for (int q = 0; q < a.nbins / 4; ++q)
+                for (int c = threadIdx.x; c < ncells; c += blockDim.x) {
+                    const uint32_t lo = cnt[(2 * q) * P + c], hi = cnt[(2 * q + 1) * P + c];
+                    __stcs(reinterpret_cast<uint4*>(out + (size_t)c * a.nbins + 4 * q),
+                           make_uint4(lo & 0xFFFFu, lo >> 16, hi & 0xFFFFu, hi >> 16));
+                }
+        } else {
+            for (int p = 0; p < a.nbins / 2; ++p)
+                for (int c = threadIdx.x; c < ncells; c += blockDim.x) {
+                    const uint32_t v = cnt[p * P + c];
+                    out[(size_t)c * a.nbins + 2 * p] = v & 0xFFFFu;
+                    out[(size_t)c * a.nbins + 2 * p + 1] = v >> 16;
+                }
+        }
     }
 }
 
@@ -783,7 +910,16 @@ cudaError_t launch_windows(const ldp_image_desc* d_descs, const ldp_image_desc* 
     ca.status = status;
     const int ncr = (max_H + ch - 1) / ch;
     const uint64_t image_words = (uint64_t)ncr * (uint64_t)ncc_max * (uint64_t)g.nbins;
-    if (image_words <= (uint64_t)kCellSmemWords) {
+    const uint64_t ncells_max = (uint64_t)ncr * (uint64_t)ncc_max;
+    const uint64_t P = (ncells_max + 31) / 32 * 32;
+    const uint64_t tw = (uint64_t)(g.nbins / 2 + 1) * P;  // words of the thread-per-cell counters
+    if (ncells_max <= (uint64_t)kCellThreads && (g.nbins & 1) == 0 && (uint64_t)ch * (uint64_t)cw <= 65535u &&
+        tw * 4u <= (uint64_t)kCellThreadSmemBytes && (uint64_t)(g.nbins / 2) * 4u * P + 16u <= 65535u) {
+        // a thread per cell, one CTA per image
+        const unsigned grid = (unsigned)(count < sms * 16 ? count : sms * 16);
+        const unsigned threads = (unsigned)P;
+        k_cell_hist_thread<<<grid, threads, sizeof(uint32_t) * (size_t)tw, s>>>(ca, count, (int)P);
+    } else if (image_words <= (uint64_t)kCellSmemWords) {
         // every cell of an image fits: one CTA per image
         const unsigned grid = (unsigned)(count < sms * 16 ? count : sms * 16);
         ca.junk = (int)image_words;
