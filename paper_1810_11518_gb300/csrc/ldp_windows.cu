@@ -6,10 +6,11 @@
 //   k_cell_hist:   one pass over the code map; a CTA owns a row of cells (a
 //                  chunk of it for wide images) -- or, when all of an
 //                  image's cells fit in shared memory, the whole image
-//                  (k_cell_hist_image) -- and counts its codes there, four
-//                  codes per lane and load, then stores the cells'
-//                  histograms (no global atomics: every cell belongs to
-//                  exactly one CTA);
+//                  (k_cell_hist_image; k_cell_hist_thread, a thread per
+//                  cell over 16-bit counters, when the cells also fit the
+//                  CTA's threads) -- and counts its codes there, then
+//                  stores the cells' histograms (no global atomics: every
+//                  cell belongs to exactly one CTA);
 //   k_window_sum:  each window histogram is the sum of its cells' (skipped
 //                  when stride = size: the cells are the windows).
 // When the column stride divides the window width (cells as wide as the
