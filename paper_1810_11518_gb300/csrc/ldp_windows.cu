@@ -435,10 +435,9 @@ struct FusedArgs {
 // Counting gives each lane one cell: units (image row, block of 32 cells) are
 // split evenly over the warps, and lane l counts the row's pixels of cell
 // 32 * block + l, so the 32 reductions of one instruction hit 32 different
-// words in 32 different banks, whatever the codes.  The code table holds,
-// per code, the byte offset of its bin pair's word row plus 16 for the upper
-// half: the reduction adds 1 << (entry mod 32) at the offset rounded down to
-// 32.  Output items (a block of 32 windows and four bins -- two pair rows --
+// words in 32 different banks, whatever the codes.  The code table holds
+// one byte per code, its bin b: the reduction adds 1 << (16 (b & 1)) to the
+// word of pair row b >> 1.  Output items (a block of 32 windows and four bins -- two pair rows --
 // or, when nbins is not a multiple of four, two bins) go to the warps in
 // turn, a lane per window: a warp reads 32 consecutive cells of a pair row per
 // load, and each cell row of a pair of window rows once.
@@ -448,20 +447,19 @@ __global__ void __launch_bounds__(kFusedThreads, 4) k_window_fused(FusedArgs a, 
     uint32_t* ring = reinterpret_cast<uint32_t*>(smem4);
     const int rs = a.row_stride, ns = a.nslots, ncp = a.ncp;
     const uint32_t b4 = 4u * (uint32_t)ncp;  // bytes between the pair rows of a ring row
-    // per code: byte offset of its bin pair's row + 16 x (bin & 1) (codes
-    // without a compact bin: pair row nbins / 2, lower half)
-    __shared__ uint16_t lut[256];
+    // bin of each code (compact bins: nbins for codes without one); one byte
+    // an entry, so a lookup meets at most two words in a bank
+    __shared__ uint8_t lut[256];
     for (int c = threadIdx.x; c < 256; c += kFusedThreads) {
         int b = (a.k >= 1) ? (int)__ldg(&g_bin_table.bin[a.k][c]) : c;
         if (b < 0) b = a.nbins;
-        lut[c] = (uint16_t)((uint32_t)(b >> 1) * b4 + 16u * (uint32_t)(b & 1));
+        lut[c] = (uint8_t)b;
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t ring_addr = (uint32_t)__cvta_generic_to_shared(ring);
     const uint32_t ring_bytes = 4u * (uint32_t)(ns * rs);
     const uint32_t stage_addr = ring_addr + ring_bytes;
     const uint32_t stage_bytes = 4u * (uint32_t)(a.group * a.stage_words);  // (checked builds)
-    const uint32_t junk_e = (uint32_t)(a.nbins >> 1) * b4;                  // table entry of the spare pair row
     // staging: window rows of windows S words apart (nbins, padded by four
     // words when nbins is a multiple of 8, so that the 16-byte stores of 8
     // consecutive windows fall in 32 different banks); the copy to HBM
@@ -512,11 +510,11 @@ __global__ void __launch_bounds__(kFusedThreads, 4) k_window_fused(FusedArgs a, 
             // one code (byte 0 of `code`): its table entry e, one reduction
             // of 1 << (e mod 32) -- 1 or 1 << 16 -- at rb + (e rounded down to 32)
             auto one = [&](uint32_t code, bool ok) {
-                uint32_t e = lut[code];
-                if (!COMPACT && !ok) e = junk_e;
+                uint32_t bin = lut[code];
+                if (!COMPACT && !ok) bin = (uint32_t)a.nbins;
                 uint32_t inc;
-                asm("shf.l.wrap.b32 %0, %1, %2, %3;" : "=r"(inc) : "r"(0u), "r"(1u), "r"(e));
-                const uint32_t addr = rb + (e & ~31u);
+                asm("shf.l.wrap.b32 %0, %1, %2, %3;" : "=r"(inc) : "r"(0u), "r"(1u), "r"(bin << 4));
+                const uint32_t addr = rb + (bin >> 1) * b4;
                 if (index_ok(addr - ring_addr < ring_bytes, a.status))
                     asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(addr), "r"(inc));
             };
