@@ -409,7 +409,7 @@ struct FusedArgs {
     int nbins, k;        // as in CellArgs (nbins even)
     int ncp;             // cells per ring row: a multiple of 32 covering the widest image's cells and windows
     int row_stride;      // ring words per cell row: (nbins / 2 + 1) x ncp (bin pairs, pair nbins / 2 takes codes without a bin)
-    int stage_words;     // staging words per window row: the widest image's windows x their stride in the staging
+    int stage_words;     // staging words per window row: the widest image's windows x nbins
     int group;           // window rows per group (G)
     int nslots;          // ring rows: (G - 1) * ph + qh
     int rows_per_band;   // window rows per work item
@@ -460,16 +460,6 @@ __global__ void __launch_bounds__(kFusedThreads, 4) k_window_fused(FusedArgs a, 
     const uint32_t ring_bytes = 4u * (uint32_t)(ns * rs);
     const uint32_t stage_addr = ring_addr + ring_bytes;
     const uint32_t stage_bytes = 4u * (uint32_t)(a.group * a.stage_words);  // (checked builds)
-    // staging: window rows of windows S words apart (nbins, padded by four
-    // words when nbins is a multiple of 8, so that the 16-byte stores of 8
-    // consecutive windows fall in 32 different banks); the copy to HBM
-    // drops the padding: thread t's first 16-byte chunk and its step, as
-    // (window, chunk in window) pairs packed into bytes
-    const int S = (a.nbins & 7) == 0 ? a.nbins + 4 : a.nbins;
-    const int nq4 = a.nbins >> 2;
-    const uint32_t cpk = nq4 == 0 ? 0u
-                                  : (uint32_t)(threadIdx.x / nq4) | (uint32_t)(threadIdx.x % nq4) << 8 |
-                                        (uint32_t)(kFusedThreads / nq4) << 16 | (uint32_t)(kFusedThreads % nq4) << 24;
     const unsigned items = (unsigned)count * (unsigned)a.bands;  // below 2^31 (checked at launch)
     for (unsigned it = blockIdx.x; it < items; it += gridDim.x) {
         const int img = (int)(it / (unsigned)a.bands), band = (int)(it - (unsigned)img * (unsigned)a.bands);
@@ -605,35 +595,33 @@ __global__ void __launch_bounds__(kFusedThreads, 4) k_window_fused(FusedArgs a, 
         // the staged window rows of the previous group -> HBM
         uint32_t* pend_dst = nullptr;
         int pend_n = 0;  // words
+        // The staging copy is laid out like the rows in HBM.  With 16-byte
+        // alignment one thread hands the block to the bulk-copy engine
+        // (cp.async.bulk, shared -> global) and the CTA goes on; the copy has
+        // read the staging before it is written again (the wait before the
+        // output phase's barrier).  Otherwise the threads copy it word by word.
         auto copy_out = [&]() {
             if (pend_n <= 0) return;
             if (vec) {
-                uint4* dst = reinterpret_cast<uint4*>(pend_dst);
-                int wi = (int)(cpk & 0xFFu), j = (int)(cpk >> 8 & 0xFFu);
-                const int dw = (int)(cpk >> 16 & 0xFFu), dj = (int)(cpk >> 24);
-                for (int e = threadIdx.x; e < (pend_n >> 2); e += kFusedThreads) {
-                    const uint32_t sa = stage_addr + 4u * (uint32_t)(wi * S + 4 * j);
-                    wi += dw;
-                    j += dj;
-                    if (j >= nq4) {
-                        j -= nq4;
-                        ++wi;
-                    }
-                    if (!index_ok(sa - stage_addr < stage_bytes, a.status)) continue;
-                    uint4 v;
-                    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
-                                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
-                                 : "r"(sa));
-                    __stcs(dst + e, v);
+                if (threadIdx.x == 0 && index_ok(4u * (uint32_t)pend_n <= stage_bytes, a.status)) {
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    asm volatile(
+                        "{\n\t.reg .u64 g;\n\tcvta.to.global.u64 g, %0;\n\t"
+                        "cp.async.bulk.global.shared::cta.bulk_group [g], [%1], %2;\n\t}" ::"l"(pend_dst),
+                        "r"(stage_addr), "r"(4u * (uint32_t)pend_n)
+                        : "memory");
+                    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
                 }
             } else {
                 for (int e = threadIdx.x; e < pend_n; e += kFusedThreads) {
-                    const int wi = e / a.nbins;  // (unaligned histograms only)
-                    const uint32_t sa = stage_addr + 4u * (uint32_t)(wi * S + (e - wi * a.nbins));
+                    const uint32_t sa = stage_addr + 4u * (uint32_t)e;
                     if (index_ok(sa - stage_addr < stage_bytes, a.status)) pend_dst[e] = lds32(sa);
                 }
             }
             pend_n = 0;
+        };
+        auto staging_free = [&]() {  // the bulk copies have read the staging
+            if (vec && threadIdx.x == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
         };
 
         // window rows wa and (two) wa + 1 of the group starting at g0 into the
@@ -647,7 +635,7 @@ __global__ void __launch_bounds__(kFusedThreads, 4) k_window_fused(FusedArgs a, 
             const int qwn = QW ? QW : a.qw;
             const int nrow = min(two ? a.ph + a.qh : a.qh, ncr - wa * a.ph);
             const uint32_t rs4 = 4u * (uint32_t)rs, so0 = rs4 * (uint32_t)sw;
-            const uint32_t srow = 4u * (uint32_t)(nwc * S);  // staging bytes per window row
+            const uint32_t srow = 4u * (uint32_t)words;  // staging bytes per window row
             const uint32_t st0 = stage_addr + srow * (uint32_t)(wa - g0), st1 = st0 + srow;
             for (int q = q_first, bb = bb_first; q < nq;) {
                 const int b = bb * 32 + lane;  // lane l takes window 32 * block + l
@@ -684,7 +672,7 @@ __global__ void __launch_bounds__(kFusedThreads, 4) k_window_fused(FusedArgs a, 
                     so += rs4;
                     if (so == ring_bytes) so = 0;
                 }
-                const uint32_t o = 4u * (uint32_t)(b * S + (QUAD ? 4 : 2) * qi);
+                const uint32_t o = 4u * (uint32_t)(b * a.nbins + (QUAD ? 4 : 2) * qi);
                 for (int h = 0; h < (two ? 2 : 1); ++h) {
                     const uint32_t sa = (h ? st1 : st0) + o, u = h ? bx : ax, v = h ? by : ay;
                     if (!index_ok(sa + (QUAD ? 16u : 8u) - stage_addr <= stage_bytes, a.status)) continue;
@@ -750,6 +738,7 @@ __global__ void __launch_bounds__(kFusedThreads, 4) k_window_fused(FusedArgs a, 
                 }
             }
             next = max(next, n1);
+            staging_free();
             __syncthreads();
             int sw = (g0 * a.ph) % ns;  // slot of the first cell row of window row wa
             for (int wa = g0; wa < g1; wa += 2) {
@@ -757,12 +746,15 @@ __global__ void __launch_bounds__(kFusedThreads, 4) k_window_fused(FusedArgs a, 
                 sw += ph2_ns;
                 if (sw >= ns) sw -= ns;
             }
+            // the staging writes, seen by the bulk-copy engine's reads
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             pend_dst = out_img + (size_t)g0 * (size_t)words;
             pend_n = (g1 - g0) * words;
         }
         __syncthreads();
-        copy_out();
+        copy_out();  // the next item's output waits for it (staging_free)
     }
+    if (threadIdx.x == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");  // every copy done
 }
 
 int gcd_int(int a, int b) {
@@ -806,9 +798,7 @@ FusedPlan fused_plan(int max_W, const WindowGeom& g) {
     const int ncp = (ncells + 31) / 32 * 32;
     if ((uint64_t)(g.nbins / 2) * 4u * (uint64_t)ncp + 16u > 65535u) return p;
     const uint64_t rs = (uint64_t)(g.nbins / 2 + 1) * (uint64_t)ncp;
-    // staging words per window row: windows (g.nbins + 4) words apart when
-    // nbins is a multiple of 8 (bank spread of the 16-byte stores)
-    const uint64_t stage = (uint64_t)nwc * (uint64_t)(g.nbins % 8 == 0 ? g.nbins + 4 : g.nbins);
+    const uint64_t stage = (uint64_t)nwc * (uint64_t)g.nbins;  // staging words per window row
     if ((uint64_t)qh * rs + stage > (uint64_t)kFusedSmemWords) return p;
     p.rs = rs;
     p.ncp = ncp;
