@@ -780,8 +780,8 @@ struct FusedPlan {
 // words per window row, window rows per group (G) and ring rows (nslots);
 // rs = 0 when the pass does not apply (stride = size, a column stride that
 // does not divide the width, windows of more than 65535 pixels -- their sums
-// would not fit a 16-bit half --, table offsets past 16 bits, or rows of cells
-// too wide for shared memory).  Groups take as many window rows as keep the
+// would not fit a 16-bit half --, or rows of cells too wide for shared
+// memory).  Groups take as many window rows as keep the
 // ring and the staging within kFusedGroupWords (up to kFusedMaxGroup); rows of
 // windows with gaps between them (row stride above the height) are not
 // grouped.
@@ -796,7 +796,6 @@ FusedPlan fused_plan(int max_W, const WindowGeom& g) {
     const int nwc = max_W <= g.ww ? 1 : (max_W - g.ww + g.sw - 1) / g.sw + 1;
     const int ncells = std::max(nwc + qw - 1, (max_W - 2) / g.sw + 1);
     const int ncp = (ncells + 31) / 32 * 32;
-    if ((uint64_t)(g.nbins / 2) * 4u * (uint64_t)ncp + 16u > 65535u) return p;
     const uint64_t rs = (uint64_t)(g.nbins / 2 + 1) * (uint64_t)ncp;
     const uint64_t stage = (uint64_t)nwc * (uint64_t)g.nbins;  // staging words per window row
     if ((uint64_t)qh * rs + stage > (uint64_t)kFusedSmemWords) return p;
