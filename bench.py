@@ -871,7 +871,7 @@ def main():
         extras["serving"] = []
         for dist in ("uneven", "faces"):
             pool = serving.RequestPool(512, dist)
-            for rate in (5000, 20000, 50000):
+            for rate in (5000, 20000, 50000, 200000):
                 with serving.Server(streams=3, max_batch=256, arena_bytes=1 << 30) as srv:
                     res = serving.run_load(srv, pool, rate, a.serve_seconds, warmup=a.serve_warmup, seed=rate)
                 res = {kk: (round(vv, 4) if isinstance(vv, float) else vv) for kk, vv in res.items()}
