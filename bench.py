@@ -754,6 +754,13 @@ def main():
 
         # ---- LBP batched on the same images ----
         lplan = ldp.BatchPlan(n, pixels, regions=(1, 1), lbp=True)
+        from paper_1810_11518_gb300 import autotune
+
+        props = torch.cuda.get_device_properties(dev)
+        lent = autotune.lookup(torch.cuda.get_device_name(dev), props.multi_processor_count, "batch", 0,
+                               "lbp+hist+codes", H * W)
+        if lent:
+            lplan.set_config(lent["variant"], lent["ctas_per_sm"])
         l_hist = torch.zeros(n * 256, dtype=torch.int32, device=dev)
         ldescs = lay.descs(d_img.data_ptr(), d_codes.data_ptr())
         ldescs["hist_offset"] = np.arange(n, dtype=np.uint64) * np.uint64(256)
@@ -769,7 +776,9 @@ def main():
         barrier()
         lms = max_over_ranks(e0.elapsed_time(e1)) / lsteps
         extras["lbp_batched"] = {"value": round(world * pixels / (lms * 1e-3) / 1e6, 3), "unit": UNIT,
-                                 "ms_per_step": round(lms, 4), "hist": "256 bins, whole image"}
+                                 "ms_per_step": round(lms, 4), "hist": "256 bins, whole image",
+                                 "variant": ldp.variant_name(lent["variant"]) if lent else "plan default",
+                                 "variant_from": "cache" if lent else "none"}
         lplan.close()
         del l_hist
 
