@@ -79,9 +79,9 @@ def dist_env():
 # profiles/k_batch_ldp_k3_512img_full.md), scaled to a launch by its pixels.
 # Valid only for the kernel sources it was taken on: any change to them
 # reports traffic as null until a new capture is recorded here.
-TRAFFIC_PER_PX = (176.721920e6 + 126.171392e6) / (512 * 640 * 490)
+TRAFFIC_PER_PX = (177.608192e6 + 125.925376e6) / (512 * 640 * 490)
 TRAFFIC_SOURCES = ("paper_1810_11518_gb300/csrc/ldp_device.cuh", "paper_1810_11518_gb300/csrc/ldp_kernels.cu")
-TRAFFIC_SHA256 = "f4e83fb588d44b3b235e692a0fc01c57385c10d6a28720ab4f328b7353bef1d7"
+TRAFFIC_SHA256 = "5fd6cc70857fe5255aa129985fbe6ba92930619c02329f41da6077077c4ea0b2"
 
 
 # Warp-instruction issue slots x 32 per input pixel of the same kernel, from

@@ -733,15 +733,29 @@ __device__ __forceinline__ void warp_tile(const Job& jb, const HistCfg& hc, int 
         const uint8_t* rp = jb.img + (size_t)u0 * P;
         const uint8_t* pf = rp + 3 * P;  // next input row to prefetch (one row ahead)
         Raw nx = load_raw(rp + 2 * P, v, W, fast_ld);
+        // LBP does far less arithmetic per row than LDP: its input rows come
+        // two ahead, the second one clamped to the image's last row (a spare
+        // load there instead of a test)
+        constexpr bool kTwoAhead = !is_ldp(MODE);
+        const uint8_t* const last_row = jb.img + (size_t)(H - 1) * P;
+        Raw nx2{};
+        if constexpr (kTwoAhead) {
+            nx2 = load_raw(u0 + 3 < H ? pf : last_row, v, W, fast_ld);
+            pf += P;  // input row u0 + 4
+        }
         Row r0, r1, r2;
         unpack(load_raw(rp, v, W, fast_ld), r0);
         unpack(load_raw(rp + P, v, W, fast_ld), r1);
         // ALWAYS: the next output row exists, so the prefetch needs no test
         auto step = [&](const Row& A, const Row& B, Row& C, int u, auto always) {
             unpack(nx, C);
-            if (decltype(always)::value ? index_ok(u + 3 < H, status)
-                                        : (u + 1 < ue && index_ok(u + 3 < H, status)))
+            if constexpr (kTwoAhead) {
+                nx = nx2;
+                nx2 = load_raw(u + 4 < H ? pf : last_row, v, W, fast_ld);
+            } else if (decltype(always)::value ? index_ok(u + 3 < H, status)
+                                               : (u + 1 < ue && index_ok(u + 3 < H, status))) {
                 nx = load_raw(pf, v, W, fast_ld);
+            }
             pf += P;
             emit(u, codes_of_row(A, B, C));
         };
