@@ -96,6 +96,25 @@ def test_all_k_and_variants(env):
                 _check(env, lay, host, d_codes, d_hist, k=k, R=4, C=3)
 
 
+def test_lbp_batch_every_variant(env):
+    """LBP through every tile variant on a batch with images of 3 to 6 rows
+    (input rows read ahead are clamped to the image's last row) beside larger
+    ones, 7x6 regions (the region-row slot variants flush per region row)."""
+    torch, ldp, oracle, synth = env
+    sizes = [(3, 40), (4, 133), (5, 7), (6, 300), (3, 3), (97, 5), (130, 260), (257, 129), (64, 1000)]
+    seeds = list(range(900, 900 + len(sizes)))
+    lay, host, d_img, d_codes, d_hist = _make(env, seeds, hist_len=7 * 6 * 256, sizes=sizes)
+    d_desc = torch.from_numpy(lay.descs(d_img.data_ptr(), d_codes.data_ptr()).view(np.uint8)).cuda()
+    d_count = torch.tensor([lay.n], dtype=torch.int32, device="cuda")
+    for v in range(ldp.num_variants()):
+        with ldp.BatchPlan(lay.n, lay.pixels, regions=(7, 6), lbp=True) as plan:
+            plan.set_config(v, 0)
+            d_codes.zero_()
+            plan.run(d_desc, d_count, d_hist)
+            _check(env, lay, host, d_codes, d_hist, R=7, C=6, compact=False, mode=oracle.MODE_LBP)
+        assert ldp.device_status() == 0, ldp.variant_name(v)
+
+
 def test_lbp_batch_and_raw_bins(env):
     torch, ldp, oracle, synth = env
     seeds = list(range(800, 816))
