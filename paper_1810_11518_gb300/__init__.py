@@ -477,8 +477,13 @@ class BatchPlan:
     sizes (the library's work list and CUDA graph live inside)."""
 
     def __init__(self, max_images: int, max_pixels: int, k: int = 3, regions=(7, 6), compact: bool = True,
-                 lbp: bool = False, graph: bool = True, code_mode: int = CODE_ABS):
+                 lbp: bool = False, graph: bool = True, code_mode: int = CODE_ABS, tuned: bool = True):
+        """tuned: take the tile variant the shipped autotune cache holds for
+        this device and workload class (k or LBP, pixels per image =
+        max_pixels / max_images), when it holds one; `config` records it.
+        set_config overrides it."""
         self.lbp = lbp
+        self.config = None
         self.k = k
         self.regions = tuple(regions)
         self.compact = bool(compact) and not lbp
@@ -489,6 +494,23 @@ class BatchPlan:
         _abi.call("ldp_batch_plan_create", ctypes.byref(h), int(max_images), int(max_pixels), int(k),
                   RegionSpec(self.regions[0], self.regions[1], int(self.compact)), flags)
         self._h = h
+        if tuned and code_mode == CODE_ABS:
+            self._apply_cache(max_images, max_pixels)
+
+    def _apply_cache(self, max_images: int, max_pixels: int) -> None:
+        from . import autotune
+
+        torch = _torch()
+        if not torch.cuda.is_available():
+            return
+        dev = torch.cuda.current_device()
+        props = torch.cuda.get_device_properties(dev)
+        ent = autotune.lookup(torch.cuda.get_device_name(dev), props.multi_processor_count, "batch",
+                              0 if self.lbp else self.k, ("lbp+" if self.lbp else "") + "hist+codes",
+                              max_pixels / max(1, max_images))
+        if ent:
+            self.set_config(ent["variant"], ent["ctas_per_sm"])
+            self.config = {"variant": ent["variant"], "ctas_per_sm": ent["ctas_per_sm"], "from": "autotune cache"}
 
     @property
     def hist_len(self) -> int:
@@ -496,6 +518,7 @@ class BatchPlan:
 
     def set_config(self, variant: int, ctas_per_sm: int = 0) -> None:
         _abi.call("ldp_batch_plan_set_config", self._h, int(variant), int(ctas_per_sm))
+        self.config = {"variant": int(variant), "ctas_per_sm": int(ctas_per_sm), "from": "set_config"}
 
     def run(self, d_descs, d_count, d_hist, stream=None) -> None:
         """d_descs: device buffer of DESC_DTYPE records; d_count: device int32
