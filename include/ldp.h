@@ -201,7 +201,8 @@ LDP_API int ldp_window_count(int n, int w, int s);
  * image (k = 0: LBP or raw bins): a code map of (H-2) x (W-2) bytes unless
  * codes_given, plus the cell histograms (cells of gcd(size, stride) pixels)
  * when the windows overlap or leave gaps and cannot take the single fused
- * pass -- which needs the column stride to divide the window width and the
+ * pass -- which needs the column stride to divide the window width, windows
+ * of at most 65535 pixels (the pass counts in 16-bit halves) and the
  * window's rows of cells to fit in shared memory.  0 on invalid arguments. */
 LDP_API uint64_t ldp_window_scratch_bytes(int H, int W, int k, ldp_window_spec ws, int codes_given);
 
