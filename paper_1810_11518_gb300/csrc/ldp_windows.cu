@@ -425,9 +425,11 @@ struct FusedArgs {
 // nslots = (G-1) ph + qh rows of a group are distinct mod nslots, rows past
 // the image stay out), then each output word (window b, bin) of the G window
 // rows is the sum over the window's qh x qw cells of their ring counters,
-// written to a shared staging copy of the G window rows, which leaves for
-// HBM as one contiguous block (16-byte stores of consecutive addresses)
-// while the next group is zeroed.  Three barriers per group.
+// written to a shared staging copy of the G window rows, laid out as in HBM,
+// which one thread hands to the bulk-copy engine as one contiguous block
+// while the next group is zeroed and counted (the threads copy it word by
+// word when the histograms are not 16-byte aligned or not whole quads of
+// bins).  Three barriers per group.
 // Counters are 16 bits, two bins to a word: bin j of cell c is half j & 1 of
 // word (j >> 1) * ncp + c of its ring row (ncp a multiple of 32), so a cell
 // of at most 65535 pixels cannot carry into the other half, and sums of such
@@ -437,10 +439,11 @@ struct FusedArgs {
 // 32 * block + l, so the 32 reductions of one instruction hit 32 different
 // words in 32 different banks, whatever the codes.  The code table holds
 // one byte per code, its bin b: the reduction adds 1 << (16 (b & 1)) to the
-// word of pair row b >> 1.  Output items (a block of 32 windows and four bins -- two pair rows --
-// or, when nbins is not a multiple of four, two bins) go to the warps in
-// turn, a lane per window: a warp reads 32 consecutive cells of a pair row per
-// load, and each cell row of a pair of window rows once.
+// word of pair row b >> 1.  Output items (a block of 32 windows and four
+// bins -- two pair rows -- or, when nbins is not a multiple of four, two
+// bins) go to the warps in turn, a lane per window: a warp reads 32
+// consecutive cells of a pair row per load, and each cell row of a pair of
+// window rows once.
 
 __global__ void __launch_bounds__(kFusedThreads, 4) k_window_fused(FusedArgs a, int count) {
     extern __shared__ uint4 smem4[];  // ring (nslots x row_stride words), then staging (group x stage_words)
