@@ -17,9 +17,10 @@
 // stride) and qh rows of cells fit in shared memory, k_window_fused does both
 // in one pass instead: a CTA walks an image's window rows top to bottom in
 // groups, counts each cell row once into a shared-memory ring that holds the
-// cell rows of the current group (one lane per cell, so the reductions of a
-// warp never meet), and writes the group's window rows straight from the
-// ring -- the cell histograms never reach HBM.
+// cell rows of the current group (16-bit counters, one lane per cell, so
+// the reductions of a warp never meet), and sums the group's window rows
+// from the ring into a staging copy that the bulk-copy engine sends to HBM
+// -- the cell histograms never reach HBM.
 // Images come from ldp_image_desc records (batches) or one record passed by
 // value (single image).
 #include <cuda_runtime.h>
